@@ -1,0 +1,621 @@
+"""Plain, slow, FP64 CPU oracle for algebraic flux correction (AFC) of P1/Q1
+finite element discretisations of 3D convection-diffusion-reaction equations.
+
+TEST INFRASTRUCTURE ONLY.  This module exists to check the CUDA library.  Only
+the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA path: it builds its
+own mesh, its own matrices and runs its own loops, in numpy/scipy, in float64.
+
+Every function follows the paper (Jha, Partl, Ahmed, Kuzmin, "An assessment of
+solvers for algebraically stabilized discretizations of convection-diffusion-
+reaction equations", arXiv 2110.15676) in its own order and notation:
+
+  * Galerkin matrices M_C, A (Sec. 2, Eq. high_order_disc and the entries m_ij,
+    a_ij that follow it), lumped mass M_L and discrete upwinding D (Sec. 2),
+    low-order operator  AA = A + D (Eq. low_order_disc);
+  * raw antidiffusive fluxes r_ij (Eq. r_decomposition), the SSP version with
+    the low-order rate (Eq. defn_r_ij_SSP, Eq. lower_time_approx), the
+    Crank-Nicolson version (Eq. flux_002) with prelimiting (Eq. prelimiting);
+  * Zalesak's limiter (Sec. 2.1.3, steps 1-4);
+  * the explicit FE-SSP update (Eq. FE-SSP) and its low-order predictor;
+  * the CN predictor (Eq. forward_euler) and the nonlinear CN system (Eq. CNZal);
+  * the monolithic convex limiter (Eq. MClimiter, Eq. u_max_min) for the
+    stationary problem (Sec. 3.1) with the operator split of Remark
+    rem:assembling_mc;
+  * the damped fixed-point iteration and stopping rules (Sec. 4, Eq. tol_formula);
+  * textbook Jacobi-preconditioned BiCGStab (van der Vorst 1992) and restarted
+    GMRES(m) with modified Gram-Schmidt and Givens rotations (Saad & Schultz
+    1986), plus a dense direct solve for tiny systems.
+
+Readings of passages the paper leaves open (numbered as in the design notes):
+  A2  Q_i^+/- are taken over the sparsity neighbours N_i \\ {i}, not all j.
+  A3  The prelimiting argument u is the CN average (u^n + u^{n-1})/2; minmod is
+      0 whenever one argument is 0.
+  A5  The damped fixed point is u <- u + omega * (AA^{-1}(f + F*(u)) - u),
+      solved in defect form.
+  A6  Delta t = CFL * min_{i not Dirichlet} m_i / AA_ii.
+  A8  MC uses the convective matrix K only for d_ij and the bar states; the
+      system matrix is K + D_K + eps*S + c*M_L.
+  A9  Reaction in the MC system is lumped (c*M_L).
+  A13 The load vector is M_L f_nodal.
+  A15 The low-order rate is 0 at Dirichlet nodes (their value does not change).
+  A16 An MC flux with d_ij = 0 is limited to 0.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+P1 = "p1"
+Q1 = "q1"
+
+
+# --------------------------------------------------------------------------
+# Mesh
+# --------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    elem: str                 # "p1" (tetrahedra) or "q1" (trilinear hexahedra)
+    xyz: np.ndarray           # (N, 3) node coordinates
+    cells: np.ndarray         # (n_cells, 4) or (n_cells, 8) node indices
+
+    @property
+    def n_nodes(self) -> int:
+        return self.xyz.shape[0]
+
+
+def structured_mesh(elem: str, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> Mesh:
+    """Uniform box grid with n = (nx, ny, nz) nodes per side, node index
+    ix + nx*(iy + ny*iz).  Q1: one hexahedron per cell, local vertex
+    k = dx + 2 dy + 4 dz.  P1: each cell cut into the six Kuhn tetrahedra that
+    share the diagonal from corner (0,0,0) to corner (1,1,1); tetrahedron for the
+    axis order (a, b, c) is {0, e_a, e_a + e_b, e_a + e_b + e_c}."""
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    nx, ny, nz = n
+    xs = [np.linspace(lo[d], hi[d], n[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    ix, iy, iz = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), np.arange(nz - 1), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    corners = []
+    for k in range(8):
+        dx, dy, dz = k & 1, (k >> 1) & 1, (k >> 2) & 1
+        corners.append((ix + dx) + nx * ((iy + dy) + ny * (iz + dz)))
+    corners = np.stack(corners, axis=1)
+    if elem == Q1:
+        cells = corners
+    elif elem == P1:
+        tets = []
+        for a, b, c in itertools.permutations(range(3)):
+            loc = [0, 1 << a, (1 << a) | (1 << b), 7]
+            tets.append(corners[:, loc])
+        cells = np.concatenate(tets, axis=0)
+    else:
+        raise ValueError(elem)
+    return Mesh(elem, xyz.astype(np.float64), cells.astype(np.int64))
+
+
+# --------------------------------------------------------------------------
+# Element matrices (Sec. 2: m_ij = (phi_j, phi_i),
+# a_ij = eps (grad phi_j, grad phi_i) + (b . grad phi_j, phi_i) + (c phi_j, phi_i))
+# --------------------------------------------------------------------------
+def p1_element_matrices(X, B):
+    """X: (E, 4, 3) vertices, B: (E, 4, 3) nodal velocity, for E tetrahedra.
+    Exact integrals for the linear basis lambda_k:
+    int lambda_i lambda_j = V (1 + delta_ij) / 20, and with b = sum_k b_k lambda_k
+    the convection entry is sum_k (b_k . grad lambda_j) V (1 + delta_ik) / 20.
+    Returns (E, 4, 4) mass M, stiffness S, convection C with C[e, i, j] = (b.grad phi_j, phi_i)."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 4, 3)
+    B = np.asarray(B, dtype=np.float64).reshape(-1, 4, 3)
+    J = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], axis=2)   # columns
+    V = np.abs(np.linalg.det(J)) / 6.0
+    Jinv = np.linalg.inv(J)
+    G = np.zeros((X.shape[0], 4, 3))
+    G[:, 1:] = Jinv                   # grad lambda_k = row k of J^{-1}, k = 1..3
+    G[:, 0] = -Jinv.sum(axis=1)
+    M = V[:, None, None] * (np.ones((4, 4)) + np.eye(4))[None] / 20.0
+    S = V[:, None, None] * np.einsum("eid,ejd->eij", G, G)
+    BG = np.einsum("ekd,ejd->ekj", B, G)      # BG[e, k, j] = b_k . grad lambda_j
+    C = np.einsum("eik,ekj->eij", M, BG)      # C[e, i, j] = sum_k M[i, k] b_k . grad lambda_j
+    return M, S, C
+
+
+_GAUSS01 = (0.5 - 0.5 / math.sqrt(3.0), 0.5 + 0.5 / math.sqrt(3.0))
+
+
+def q1_element_matrices(X, B):
+    """Trilinear elements on the reference cube [0,1]^3, vertex k = dx + 2dy + 4dz,
+    2x2x2 Gauss quadrature (exact on parallelepipeds for mass, stiffness and
+    convection with a trilinearly interpolated velocity).  X, B: (E, 8, 3)."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 8, 3)
+    B = np.asarray(B, dtype=np.float64).reshape(-1, 8, 3)
+    E = X.shape[0]
+    M = np.zeros((E, 8, 8)); S = np.zeros((E, 8, 8)); C = np.zeros((E, 8, 8))
+    bits = np.array([[k & 1, (k >> 1) & 1, (k >> 2) & 1] for k in range(8)], dtype=np.float64)
+    for xi in itertools.product(_GAUSS01, repeat=3):
+        w = 0.125
+        f1 = [np.where(bits[:, d] == 1, xi[d], 1.0 - xi[d]) for d in range(3)]
+        df = [np.where(bits[:, d] == 1, 1.0, -1.0) for d in range(3)]
+        phi = f1[0] * f1[1] * f1[2]                                        # (8,)
+        dphi_ref = np.stack([df[0] * f1[1] * f1[2], f1[0] * df[1] * f1[2], f1[0] * f1[1] * df[2]], axis=1)
+        J = np.einsum("eka,kd->ead", X, dphi_ref)     # J[e, a, d] = d x_a / d xi_d
+        detJ = np.linalg.det(J)
+        dphi = np.einsum("kd,eda->eka", dphi_ref, np.linalg.inv(J))   # grad_x phi_k = J^{-T} grad_xi phi_k
+        bq = np.einsum("k,eka->ea", phi, B)
+        wd = (w * np.abs(detJ))[:, None, None]
+        M += wd * np.outer(phi, phi)[None]
+        S += wd * np.einsum("eia,eja->eij", dphi, dphi)
+        C += wd * np.einsum("i,eja,ea->eij", phi, dphi, bq)      # C[e, i, j] = (b . grad phi_j) phi_i
+    return M, S, C
+
+
+# --------------------------------------------------------------------------
+# Problem assembly
+# --------------------------------------------------------------------------
+@dataclass
+class Problem:
+    mesh: Mesh
+    eps: float
+    c: float
+    b: np.ndarray                 # (N, 3) nodal velocity
+    f_nodal: np.ndarray           # (N,)
+    dir_mask: np.ndarray          # (N,) bool
+    u_dir: np.ndarray             # (N,) Dirichlet values (used where dir_mask)
+    limiter_family: str = "fct"   # "fct" (Zalesak) or "mc"
+    # assembled quantities
+    MC: sp.csr_matrix = None      # consistent mass
+    S: sp.csr_matrix = None       # stiffness (grad phi_j, grad phi_i)
+    K: sp.csr_matrix = None       # convection (b . grad phi_j, phi_i)
+    A: sp.csr_matrix = None       # operator whose off-diagonals define D
+    D: sp.csr_matrix = None       # discrete upwinding
+    AA: sp.csr_matrix = None      # low-order operator (system operator for MC)
+    mL: np.ndarray = None         # lumped mass m_i
+    f: np.ndarray = None          # load vector M_L f_nodal (A13)
+    pairs: tuple = None           # directed off-diagonal pairs (I, J) with m_IJ != 0
+    extra: dict = field(default_factory=dict)
+
+
+def assemble(mesh: Mesh, eps: float, b, c: float, f_nodal, dir_mask, u_dir, limiter_family="fct") -> Problem:
+    N = mesh.n_nodes
+    b = np.broadcast_to(np.asarray(b, dtype=np.float64), (N, 3)).copy()
+    f_nodal = np.broadcast_to(np.asarray(f_nodal, dtype=np.float64), (N,)).copy()
+    dir_mask = np.asarray(dir_mask, dtype=bool).copy()
+    u_dir = np.broadcast_to(np.asarray(u_dir, dtype=np.float64), (N,)).copy()
+    elmat = p1_element_matrices if mesh.elem == P1 else q1_element_matrices
+    nl = mesh.cells.shape[1]
+    cells = mesh.cells
+    Me, Se, Ce = elmat(mesh.xyz[cells], b[cells])
+    rows = np.repeat(cells, nl, axis=1).ravel()           # row index of entry (e, i, j) is cells[e, i]
+    cols = np.tile(cells, (1, nl)).ravel()                # column index is cells[e, j]
+    MC = sp.csr_matrix((Me.ravel(), (rows, cols)), shape=(N, N))
+    S = sp.csr_matrix((Se.ravel(), (rows, cols)), shape=(N, N))
+    K = sp.csr_matrix((Ce.ravel(), (rows, cols)), shape=(N, N))
+    for X in (MC, S, K):
+        X.sum_duplicates(); X.sort_indices()
+    # all three share the element pattern; make the stored patterns identical
+    pattern = (abs(MC) + abs(S) + abs(K)).tocsr()
+    pattern.data[:] = 1.0
+    MC = _on_pattern(MC, pattern); S = _on_pattern(S, pattern); K = _on_pattern(K, pattern)
+    mL = np.asarray(MC.sum(axis=1)).ravel()                   # m_i = sum_j m_ij
+    if limiter_family == "fct":
+        A = (eps * S + K + c * MC).tocsr()                    # a_ij of Sec. 2
+        D = discrete_upwinding(A)
+        AA = (A + D).tocsr()
+    elif limiter_family == "mc":
+        # Remark rem:assembling_mc with readings A8, A9: flux correction for the
+        # eps = 0, c = 0 operator, unlimited diffusion and (lumped) reaction.
+        A = K.copy()
+        D = discrete_upwinding(K)
+        AA = (K + D + eps * S + sp.diags(c * mL)).tocsr()
+    else:
+        raise ValueError(limiter_family)
+    AA = _on_pattern(AA, pattern)
+    I, J = _offdiag_pairs(MC)
+    prob = Problem(mesh, eps, c, b, f_nodal, dir_mask, u_dir, limiter_family,
+                   MC=MC, S=S, K=K, A=A, D=D, AA=AA, mL=mL, f=mL * f_nodal, pairs=(I, J))
+    return prob
+
+
+def _on_pattern(X, pattern):
+    """Return X with exactly the stored pattern of `pattern` (explicit zeros kept)."""
+    X = X.tocsr()
+    P = pattern.tocoo()
+    vals = np.asarray(X[P.row, P.col]).ravel()
+    Y = sp.csr_matrix((vals, (P.row, P.col)), shape=X.shape)
+    Y.sort_indices()
+    return Y
+
+
+def _offdiag_pairs(MC):
+    """Directed pairs (i, j), i != j, with m_ij != 0: the neighbour sets N_i of Eq. u_max_min."""
+    C = MC.tocoo()
+    keep = (C.row != C.col) & (C.data != 0.0)
+    return C.row[keep].astype(np.int64), C.col[keep].astype(np.int64)
+
+
+def entries(X, I, J):
+    return np.asarray(X[I, J]).ravel()
+
+
+def discrete_upwinding(A):
+    """D of Sec. 2: d_ij = -max{a_ij, 0, a_ji} (i != j), d_ii = -sum_{j != i} d_ij."""
+    A = A.tocsr()
+    C = A.tocoo()
+    off = C.row != C.col
+    I, Jc = C.row[off], C.col[off]
+    aij = C.data[off]
+    aji = entries(A, Jc, I)
+    dij = -np.maximum(np.maximum(aij, 0.0), aji)
+    N = A.shape[0]
+    Doff = sp.csr_matrix((dij, (I, Jc)), shape=(N, N))
+    diag = -np.asarray(Doff.sum(axis=1)).ravel()
+    return (Doff + sp.diags(diag)).tocsr()
+
+
+def cfl_timestep(prob: Problem, cfl: float) -> float:
+    """Reading A6: Delta t = CFL * min over non-Dirichlet i of m_i / AA_ii."""
+    diag = prob.AA.diagonal()
+    free = ~prob.dir_mask
+    return float(cfl * np.min(prob.mL[free] / diag[free]))
+
+
+# --------------------------------------------------------------------------
+# Zalesak's limiter (Sec. 2.1.3)
+# --------------------------------------------------------------------------
+def zalesak_limiter(prob: Problem, r, u_tilde, dt, mode="zalesak"):
+    """r: antidiffusive fluxes r_ij on the directed pairs (I, J).
+    mode "zalesak": steps 1-4 of Sec. 2.1.3; "galerkin": alpha = 1; "none": alpha = 0.
+    Returns alpha on the pairs and the node arrays P+, P-, Q+, Q-, R+, R-."""
+    I, J = prob.pairs
+    N = prob.mesh.n_nodes
+    # step 1
+    Pp = np.bincount(I, weights=np.maximum(r, 0.0), minlength=N)
+    Pm = np.bincount(I, weights=np.minimum(r, 0.0), minlength=N)
+    # step 2 (reading A2: j over the neighbours N_i \ {i})
+    Qp = np.zeros(N); Qm = np.zeros(N)
+    np.maximum.at(Qp, I, u_tilde[J] - u_tilde[I])
+    np.minimum.at(Qm, I, u_tilde[J] - u_tilde[I])
+    # step 3
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Rp = np.where(Pp != 0.0, np.minimum(1.0, prob.mL * Qp / (dt * Pp)), 1.0)
+        Rm = np.where(Pm != 0.0, np.minimum(1.0, prob.mL * Qm / (dt * Pm)), 1.0)
+    Rp[prob.dir_mask] = 1.0
+    Rm[prob.dir_mask] = 1.0
+    # step 4
+    alpha = np.where(r > 0.0, np.minimum(Rp[I], Rm[J]), np.minimum(Rm[I], Rp[J]))
+    if mode == "galerkin":
+        alpha = np.ones_like(r)
+    elif mode == "none":
+        alpha = np.zeros_like(r)
+    elif mode != "zalesak":
+        raise ValueError(mode)
+    return alpha, dict(Pp=Pp, Pm=Pm, Qp=Qp, Qm=Qm, Rp=Rp, Rm=Rm)
+
+
+def limited_sum(prob: Problem, alpha, r):
+    """F*_i = sum_{j != i} alpha_ij r_ij (Eq. definition_of_f_i)."""
+    I, _ = prob.pairs
+    return np.bincount(I, weights=alpha * r, minlength=prob.mesh.n_nodes)
+
+
+# --------------------------------------------------------------------------
+# Explicit SSP schemes with Zalesak FCT (Sec. 2.1.2)
+# --------------------------------------------------------------------------
+def low_order_rate(prob: Problem, u):
+    """Eq. lower_time_approx: udot^L = M_L^{-1}(f - AA u); 0 at Dirichlet nodes (A15)."""
+    udot = (prob.f - prob.AA @ u) / prob.mL
+    udot[prob.dir_mask] = 0.0
+    return udot
+
+
+def ssp_fluxes(prob: Problem, u, udot):
+    """Eq. defn_r_ij_SSP: r_ij = m_ij (udot_i - udot_j) + d_ij (u_j - u_i)."""
+    I, J = prob.pairs
+    m = entries(prob.MC, I, J)
+    d = entries(prob.D, I, J)
+    return m * (udot[I] - udot[J]) + d * (u[J] - u[I])
+
+
+def fe_ssp_stage(prob: Problem, u, dt, mode="zalesak", want=False):
+    """One forward-Euler FCT stage, Eq. FE-SSP, with the predictor
+    u~ = u + dt M_L^{-1}(f - AA u) constrained to the Dirichlet data."""
+    udot = low_order_rate(prob, u)
+    u_tilde = u + dt * (prob.f - prob.AA @ u) / prob.mL
+    u_tilde[prob.dir_mask] = prob.u_dir[prob.dir_mask]
+    r = ssp_fluxes(prob, u, udot)
+    alpha, lim = zalesak_limiter(prob, r, u_tilde, dt, mode)
+    Fstar = limited_sum(prob, alpha, r)
+    u_new = u + dt * (prob.f + Fstar - prob.AA @ u) / prob.mL
+    u_new[prob.dir_mask] = prob.u_dir[prob.dir_mask]
+    if want:
+        return u_new, dict(udot=udot, u_tilde=u_tilde, r=r, alpha=alpha, Fstar=Fstar, **lim)
+    return u_new
+
+
+def ssp_step(prob: Problem, u, dt, order=3, mode="zalesak"):
+    """order 2: Heun's method as written in Sec. 2.1.2, u^n = (u^{n,0} + u^{n,2}) / 2.
+    order 3: the three-stage Shu-Osher SSP scheme (reading A1), each stage one
+    forward-Euler FCT update."""
+    if order == 2:
+        u1 = fe_ssp_stage(prob, u, dt, mode)
+        u2 = fe_ssp_stage(prob, u1, dt, mode)
+        return 0.5 * (u + u2)
+    if order == 3:
+        u1 = fe_ssp_stage(prob, u, dt, mode)
+        u2 = 0.75 * u + 0.25 * fe_ssp_stage(prob, u1, dt, mode)
+        return u / 3.0 + (2.0 / 3.0) * fe_ssp_stage(prob, u2, dt, mode)
+    raise ValueError(order)
+
+
+# --------------------------------------------------------------------------
+# Crank-Nicolson FCT (Sec. 2.1.1), nonlinear fixed point (Sec. 4)
+# --------------------------------------------------------------------------
+def minmod(a, b):
+    """Eq. prelimiting: 0 if ab < 0, min if both > 0, max if both < 0 (0 otherwise, A3)."""
+    out = np.zeros_like(a)
+    pos = (a > 0.0) & (b > 0.0)
+    neg = (a < 0.0) & (b < 0.0)
+    out[pos] = np.minimum(a[pos], b[pos])
+    out[neg] = np.maximum(a[neg], b[neg])
+    return out
+
+
+def cn_fluxes(prob: Problem, u_new, u_old, dt, prelimit=True):
+    """Eq. flux_002, then Eq. prelimiting with L = 2 applied to the CN average (A3)."""
+    I, J = prob.pairs
+    m = entries(prob.MC, I, J)
+    d = entries(prob.D, I, J)
+    r = (m / dt) * ((u_new[I] - u_old[I]) - (u_new[J] - u_old[J])) \
+        + 0.5 * d * ((u_new[J] + u_old[J]) - (u_new[I] + u_old[I]))
+    if prelimit:
+        ubar = 0.5 * (u_new + u_old)
+        r = minmod(r, 2.0 * d * (ubar[J] - ubar[I]))
+    return r
+
+
+def cn_system_matrix(prob: Problem, dt):
+    """M_L / dt + AA / 2 with the Dirichlet rows replaced by identity rows."""
+    B = (sp.diags(prob.mL / dt) + 0.5 * prob.AA).tolil()
+    for i in np.flatnonzero(prob.dir_mask):
+        B.rows[i] = [i]; B.data[i] = [1.0]
+    return B.tocsr()
+
+
+def cn_step(prob: Problem, u_old, dt, tol=1e-10, max_outer=100, omega=1.0, prelimit=True,
+            mode="zalesak", ksp="bicgstab", ksp_atol=1e-12, ksp_rtol=0.0, ksp_maxit=1000,
+            gmres_restart=20, fixed_iterations=None):
+    """One step of nonlinear Zal+CN: solve Eq. CNZal by the damped fixed point of Sec. 4,
+    u <- u + omega * B^{-1} res(u),  res(u) = b0 + F*(u, u_old) - B u,  B = M_L/dt + AA/2,
+    stop when ||res||_2 < sqrt(N) tol (Eq. tol_formula).  Q+/- come from the CN predictor
+    Eq. forward_euler, which stays fixed for the whole step.  The initial guess is u_old.
+    Returns (u_new, stats)."""
+    N = prob.mesh.n_nodes
+    dirm = prob.dir_mask
+    u_tilde = u_old - 0.5 * dt * (prob.AA @ u_old - prob.f) / prob.mL
+    u_tilde[dirm] = prob.u_dir[dirm]
+    b0 = prob.mL / dt * u_old - 0.5 * (prob.AA @ u_old) + prob.f     # (f^n + f^{n-1})/2 = f
+    Bsys = cn_system_matrix(prob, dt)
+    dinv = 1.0 / Bsys.diagonal()
+    u = u_old.copy()
+    u[dirm] = prob.u_dir[dirm]
+    stats = dict(outer_its=0, inner_its=0, res_hist=[])
+    for it in range(max_outer + 1):
+        r = cn_fluxes(prob, u, u_old, dt, prelimit)
+        alpha, _ = zalesak_limiter(prob, r, u_tilde, dt, mode)
+        Fstar = limited_sum(prob, alpha, r)
+        res = b0 + Fstar - (prob.mL / dt * u + 0.5 * (prob.AA @ u))
+        res[dirm] = 0.0
+        R = float(np.linalg.norm(res))
+        stats["res_hist"].append(R)
+        if fixed_iterations is None:
+            if R < math.sqrt(N) * tol or it == max_outer:
+                break
+        elif it == fixed_iterations:
+            break
+        delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
+        stats["inner_its"] += kst["its"]
+        u = u + omega * delta
+        stats["outer_its"] += 1
+    stats["res_final"] = stats["res_hist"][-1]
+    stats["converged"] = stats["res_final"] < math.sqrt(N) * tol
+    return u, stats
+
+
+# --------------------------------------------------------------------------
+# Monolithic convex limiter, stationary problem (Sec. 2.2, Sec. 3.1)
+# --------------------------------------------------------------------------
+def mc_bounds(prob: Problem, u):
+    """Eq. u_max_min over N_i (which contains i)."""
+    I, J = prob.pairs
+    umax = u.copy(); umin = u.copy()
+    np.maximum.at(umax, I, u[J])
+    np.minimum.at(umin, I, u[J])
+    return umax, umin
+
+
+def mc_limited_fluxes(prob: Problem, u, mode="mc"):
+    """Eq. MClimiter with r_ij = d_ij (u_j - u_i) (Sec. 3.1), bar states
+    2 d_ij ubar_ij = d_ij (u_i + u_j) + a_ij (u_j - u_i), a_ij the convective
+    entries (A8).  Returns r*_ij on the directed pairs and the bounds."""
+    I, J = prob.pairs
+    d = entries(prob.D, I, J)
+    aij = entries(prob.K, I, J)
+    aji = entries(prob.K, J, I)
+    r = d * (u[J] - u[I])
+    if mode == "galerkin":
+        return r, {}
+    if mode == "none":
+        return np.zeros_like(r), {}
+    umax, umin = mc_bounds(prob, u)
+    rstar = np.zeros_like(r)
+    nz = d != 0.0                                        # A16
+    dI, uI, uJ = d[nz], u[I[nz]], u[J[nz]]
+    ubar_ij = (dI * (uI + uJ) + aij[nz] * (uJ - uI)) / (2.0 * dI)
+    ubar_ji = (dI * (uJ + uI) + aji[nz] * (uI - uJ)) / (2.0 * dI)
+    rr = r[nz]
+    up = np.minimum(rr, np.minimum(2.0 * dI * (ubar_ij - umax[I[nz]]), 2.0 * dI * (umin[J[nz]] - ubar_ji)))
+    dn = np.maximum(rr, np.maximum(2.0 * dI * (ubar_ij - umin[I[nz]]), 2.0 * dI * (umax[J[nz]] - ubar_ji)))
+    rstar[nz] = np.where(rr > 0.0, up, dn)
+    return rstar, dict(umax=umax, umin=umin, r=r)
+
+
+def stationary_system_matrix(prob: Problem):
+    B = prob.AA.tolil()
+    for i in np.flatnonzero(prob.dir_mask):
+        B.rows[i] = [i]; B.data[i] = [1.0]
+    return B.tocsr()
+
+
+def mc_stationary(prob: Problem, u0=None, tol=1e-10, max_outer=1000, omega=0.5, mode="mc",
+                  ksp="gmres", ksp_atol=1e-12, ksp_rtol=0.0, ksp_maxit=1000, gmres_restart=20,
+                  fixed_iterations=None):
+    """Sec. 3.1 with the damped fixed point of Sec. 4 (reading A5):
+    res = f + F*(u) - AA u, AA delta = res, u <- u + omega delta,
+    stop when ||res||_2 < sqrt(N) tol."""
+    N = prob.mesh.n_nodes
+    dirm = prob.dir_mask
+    u = np.zeros(N) if u0 is None else np.array(u0, dtype=np.float64)
+    u[dirm] = prob.u_dir[dirm]
+    Bsys = stationary_system_matrix(prob)
+    dinv = 1.0 / Bsys.diagonal()
+    stats = dict(outer_its=0, inner_its=0, res_hist=[])
+    for it in range(max_outer + 1):
+        rstar, _ = mc_limited_fluxes(prob, u, mode)
+        Fstar = limited_sum(prob, np.ones_like(rstar), rstar)
+        res = prob.f + Fstar - prob.AA @ u
+        res[dirm] = 0.0
+        R = float(np.linalg.norm(res))
+        stats["res_hist"].append(R)
+        if fixed_iterations is None:
+            if R < math.sqrt(N) * tol or it == max_outer:
+                break
+        elif it == fixed_iterations:
+            break
+        delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
+        stats["inner_its"] += kst["its"]
+        u = u + omega * delta
+        stats["outer_its"] += 1
+    stats["res_final"] = stats["res_hist"][-1]
+    stats["converged"] = stats["res_final"] < math.sqrt(N) * tol
+    return u, stats
+
+
+# --------------------------------------------------------------------------
+# Linear solvers (Sec. 4: rtol = 0, stop when the Euclidean residual norm < atol)
+# --------------------------------------------------------------------------
+def krylov_solve(B, rhs, dinv, ksp, atol, rtol, maxit, restart):
+    if ksp == "bicgstab":
+        return bicgstab(B, rhs, dinv, atol, rtol, maxit)
+    if ksp == "gmres":
+        return gmres(B, rhs, dinv, restart, atol, rtol, maxit)
+    if ksp == "direct":
+        return dense_solve(B, rhs), dict(its=1)
+    raise ValueError(ksp)
+
+
+def _stop(norm_r, norm_r0, atol, rtol):
+    return norm_r < max(atol, rtol * norm_r0)
+
+
+def bicgstab(B, b, dinv, atol=1e-12, rtol=0.0, maxit=1000):
+    """Preconditioned BiCGStab (van der Vorst 1992) with the Jacobi preconditioner
+    M^{-1} = diag(dinv) applied to the search directions, x0 = 0.  The stopping test
+    uses the true-residual recurrence ||r||_2."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    rhat = r.copy()
+    n0 = float(np.linalg.norm(r))
+    if _stop(n0, n0, atol, rtol):
+        return x, dict(its=0, res=n0)
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b); p = np.zeros_like(b)
+    its = 0
+    nr = n0
+    while its < maxit:
+        its += 1
+        rho = float(rhat @ r)
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        phat = dinv * p
+        v = B @ phat
+        alpha = rho / float(rhat @ v)
+        s = r - alpha * v
+        ns = float(np.linalg.norm(s))
+        if _stop(ns, n0, atol, rtol):
+            x = x + alpha * phat
+            nr = ns
+            break
+        shat = dinv * s
+        t = B @ shat
+        omega = float(t @ s) / float(t @ t)
+        x = x + alpha * phat + omega * shat
+        r = s - omega * t
+        nr = float(np.linalg.norm(r))
+        if _stop(nr, n0, atol, rtol):
+            break
+        rho_old = rho
+    return x, dict(its=its, res=nr)
+
+
+def gmres(B, b, dinv, m=20, atol=1e-12, rtol=0.0, maxit=1000):
+    """Restarted GMRES(m) (Saad & Schultz 1986), right preconditioned with the Jacobi
+    preconditioner: B M^{-1} y = b, x = M^{-1} y; modified Gram-Schmidt Arnoldi, Givens
+    rotations, x0 = 0.  'its' counts Arnoldi steps (one product with B each)."""
+    n = b.shape[0]
+    x = np.zeros(n)
+    r = b.copy()
+    beta = float(np.linalg.norm(r))
+    n0 = beta
+    its = 0
+    if _stop(beta, n0, atol, rtol):
+        return x, dict(its=0, res=beta)
+    while its < maxit:
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m); sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        V[0] = r / beta
+        g[0] = beta
+        k_used = 0
+        for k in range(m):
+            its += 1
+            w = B @ (dinv * V[k])
+            for i in range(k + 1):
+                H[i, k] = float(w @ V[i])
+                w = w - H[i, k] * V[i]
+            H[k + 1, k] = float(np.linalg.norm(w))
+            if H[k + 1, k] != 0.0:
+                V[k + 1] = w / H[k + 1, k]
+            for i in range(k):                          # apply earlier rotations
+                hi, hi1 = H[i, k], H[i + 1, k]
+                H[i, k] = cs[i] * hi + sn[i] * hi1
+                H[i + 1, k] = -sn[i] * hi + cs[i] * hi1
+            denom = math.hypot(H[k, k], H[k + 1, k])
+            cs[k] = H[k, k] / denom
+            sn[k] = H[k + 1, k] / denom
+            H[k, k] = denom
+            H[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            k_used = k + 1
+            if _stop(abs(g[k + 1]), n0, atol, rtol) or its >= maxit:
+                break
+        y = np.zeros(k_used)
+        for i in range(k_used - 1, -1, -1):             # back substitution
+            y[i] = (g[i] - H[i, i + 1:k_used] @ y[i + 1:k_used]) / H[i, i]
+        x = x + dinv * (V[:k_used].T @ y)
+        r = b - B @ x
+        beta = float(np.linalg.norm(r))
+        if _stop(beta, n0, atol, rtol):
+            break
+    return x, dict(its=its, res=beta)
+
+
+def dense_solve(B, b):
+    """Direct solve for tiny systems (Gaussian elimination with partial pivoting)."""
+    return np.linalg.solve(B.toarray(), b)

@@ -1,0 +1,127 @@
+"""Seeded synthetic inputs for the AFC hot path.
+
+This module only produces input data: node coordinates of uniform box grids,
+nodal velocity fields, initial data, sources and Dirichlet sets.  It holds none
+of the method's arithmetic (no matrices, fluxes or limiters), so both the CUDA
+library and the CPU oracle can be fed from it.
+
+The workloads mirror the 3D tests of the paper (uniform cube grids, rotating or
+constant convection, small diffusion, data in [0, 1]):
+
+* ``rotating_transient``: unit cube, b = (0.5 - y, x - 0.5, 0) (the rotating
+  field of the paper's rotating-shapes example), smooth cosine hump of radius
+  0.15 centred at (0.5, 0.75, 0.5), f = 0, c = 0, homogeneous Dirichlet data on
+  the whole boundary.
+* ``stationary_inflow``: unit cube, b = (1, -0.5, 0.25), c = 1, f = 1 on the
+  closed cube [0.25, 0.5]^3, Dirichlet data on the inflow faces x = 0, y = 1,
+  z = 0 with value 1 where x = 0 and y < 0.5, else 0.
+* ``random_transient``: a seeded random instance (node count per side, eps,
+  constant unit velocity, hump centre) for batched runs.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+P1 = "p1"
+Q1 = "q1"
+
+
+@dataclass
+class Workload:
+    name: str
+    elem: str
+    n: tuple            # nodes per side (nx, ny, nz)
+    lo: tuple
+    hi: tuple
+    eps: float
+    c: float
+    b: np.ndarray       # (N, 3) nodal velocity
+    f: np.ndarray       # (N,) nodal source
+    u0: np.ndarray      # (N,) initial data / initial guess
+    dir_mask: np.ndarray  # (N,) uint8
+    u_dir: np.ndarray   # (N,) Dirichlet values
+
+    @property
+    def n_nodes(self) -> int:
+        return int(np.prod(self.n))
+
+
+def grid_coords(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """(N, 3) node coordinates, node index ix + nx*(iy + ny*iz)."""
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    xs = [np.linspace(lo[d], hi[d], n[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def grid_index(n):
+    """Integer (ix, iy, iz) of every node."""
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    iz, iy, ix = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return ix.ravel(), iy.ravel(), iz.ravel()
+
+
+def boundary_mask(n) -> np.ndarray:
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    ix, iy, iz = grid_index(n)
+    m = (ix == 0) | (ix == n[0] - 1) | (iy == 0) | (iy == n[1] - 1) | (iz == 0) | (iz == n[2] - 1)
+    return m.astype(np.uint8)
+
+
+def cosine_hump(xyz, center=(0.5, 0.75, 0.5), radius=0.15) -> np.ndarray:
+    """0.5 (1 + cos(pi r / radius)) for r <= radius, else 0; values in [0, 1]."""
+    r = np.linalg.norm(xyz - np.asarray(center)[None, :], axis=1)
+    return np.where(r <= radius, 0.5 * (1.0 + np.cos(np.pi * np.minimum(r, radius) / radius)), 0.0)
+
+
+def rotating_b(xyz) -> np.ndarray:
+    return np.stack([0.5 - xyz[:, 1], xyz[:, 0] - 0.5, np.zeros(len(xyz))], axis=1)
+
+
+def rotating_transient(elem: str, n: int, eps: float = 1e-6) -> Workload:
+    xyz = grid_coords(n)
+    N = len(xyz)
+    return Workload(
+        name=f"rotating_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
+        eps=eps, c=0.0, b=rotating_b(xyz), f=np.zeros(N), u0=cosine_hump(xyz),
+        dir_mask=boundary_mask(n), u_dir=np.zeros(N))
+
+
+def stationary_inflow(elem: str, n: int, eps: float = 1e-8, c: float = 1.0,
+                      b=(1.0, -0.5, 0.25)) -> Workload:
+    xyz = grid_coords(n)
+    N = len(xyz)
+    ix, iy, iz = grid_index(n)
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    # inflow faces for b = (1, -0.5, 0.25): x = 0, y = 1, z = 0 (closed faces)
+    inflow = (ix == 0) | (iy == n - 1) | (iz == 0)
+    u_dir = np.where((ix == 0) & (y < 0.5), 1.0, 0.0)
+    f = np.where((x >= 0.25) & (x <= 0.5) & (y >= 0.25) & (y <= 0.5) & (z >= 0.25) & (z <= 0.5), 1.0, 0.0)
+    bb = np.tile(np.asarray(b, dtype=np.float64), (N, 1))
+    u0 = np.where(inflow, u_dir, 0.0)
+    return Workload(
+        name=f"stationary_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
+        eps=eps, c=c, b=bb, f=f, u0=u0, dir_mask=inflow.astype(np.uint8), u_dir=u_dir)
+
+
+def random_transient(rng: np.random.Generator, elem: str = Q1, n_range=(17, 49)) -> Workload:
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    eps = float(10.0 ** rng.uniform(-8.0, -4.0))
+    v = rng.normal(size=3)
+    v /= np.linalg.norm(v)
+    center = rng.uniform(0.3, 0.7, size=3)
+    xyz = grid_coords(n)
+    N = len(xyz)
+    return Workload(
+        name=f"random_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
+        eps=eps, c=0.0, b=np.tile(v, (N, 1)), f=np.zeros(N), u0=cosine_hump(xyz, center),
+        dir_mask=boundary_mask(n), u_dir=np.zeros(N))
+
+
+def random_field(rng: np.random.Generator, N: int, lo=0.0, hi=1.0) -> np.ndarray:
+    return rng.uniform(lo, hi, size=N)
