@@ -1,0 +1,214 @@
+/*
+ * afc.h - C ABI of libafc, a GB300 (sm_103a) library for algebraic flux
+ * correction (AFC) of P1/Q1 finite element discretisations of 3D
+ * convection-diffusion-reaction (CDR) equations.
+ *
+ * Method: Jha, Partl, Ahmed, Kuzmin, "An assessment of solvers for algebraically
+ * stabilized discretizations of convection-diffusion-reaction equations"
+ * (arXiv 2110.15676).  Section / equation names below refer to that paper.
+ *
+ * Conventions shared by every call
+ *  - Every call returns an int status (afc_status).  No C++ exception crosses
+ *    this boundary.  afc_status_str() gives a message; afc_last_error() gives
+ *    the detail of the last failure on the calling thread.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Pointers
+ *    documented as "device" must point to memory on the problem's device.
+ *  - The library owns every device buffer it allocates, until afc_destroy().
+ *  - All device work is enqueued on the stream given at creation (NULL = the
+ *    legacy default stream).  Calls that return values to host memory
+ *    synchronise that stream before returning.
+ *  - A problem handle is used by one host thread at a time.
+ *  - Structured meshes number nodes ix + nx*(iy + ny*iz) (x fastest).
+ *  - All floating point data is IEEE double unless stated otherwise.
+ */
+#ifndef AFC_H
+#define AFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afc_problem_s* afc_problem;
+
+typedef enum {
+  AFC_OK = 0,
+  AFC_NOT_CONVERGED = 1,  /* result valid (last iterate), tolerance not met   */
+  AFC_E_INVALID = -1,     /* bad argument or size                             */
+  AFC_E_OOM = -2,         /* device allocation failed                         */
+  AFC_E_CUDA = -3,        /* CUDA runtime error (detail in afc_last_error)    */
+  AFC_E_NAN = -4,         /* NaN or Inf met in a residual or solver scalar    */
+  AFC_E_TIMEOUT = -5,     /* a bounded device wait expired                    */
+  AFC_E_STATE = -6        /* call out of order (e.g. step before assemble)    */
+} afc_status;
+
+typedef enum { AFC_P1 = 0, AFC_Q1 = 1 } afc_elem;     /* tetrahedra / trilinear hexahedra */
+
+/* Which matrix family afc_assemble builds.
+ * FCT: A = eps*S + K + c*M_C (Sec. 2), D from A, AA = A + D.
+ * MC : flux correction of the eps = 0, c = 0 operator (Remark rem:assembling_mc):
+ *      D from the convective matrix K, AA = K + D + eps*S + c*M_L (lumped reaction). */
+typedef enum { AFC_FAMILY_FCT = 0, AFC_FAMILY_MC = 1 } afc_family;
+
+typedef enum { AFC_SSP2 = 0, AFC_SSP3 = 1, AFC_CN_NONLINEAR = 2 } afc_scheme;
+typedef enum { AFC_LIM_NONE = 0, AFC_LIM_GALERKIN = 1, AFC_LIM_ZALESAK = 2, AFC_LIM_MC = 3 } afc_limiter;
+typedef enum { AFC_KSP_BICGSTAB = 0, AFC_KSP_GMRES = 1 } afc_ksp;
+typedef enum { AFC_FP64 = 0, AFC_MIXED = 1 } afc_precision;
+
+/* Matrices afc_export_csr can return. */
+typedef enum {
+  AFC_MAT_MC = 0,      /* consistent mass m_ij                                     */
+  AFC_MAT_A = 1,       /* matrix whose off-diagonals define D (FCT: A, MC: K)       */
+  AFC_MAT_D = 2,       /* discrete upwinding d_ij                                   */
+  AFC_MAT_LOW = 3,     /* low-order operator AA = A + D (no Dirichlet rows applied) */
+  AFC_MAT_K = 4,       /* convection (b . grad phi_j, phi_i)                        */
+  AFC_MAT_S = 5        /* stiffness (grad phi_j, grad phi_i)                        */
+} afc_matrix;
+
+typedef struct {
+  int64_t n_nodes;        /* N                                                     */
+  int64_t nnz;            /* stored pattern entries (pairs with m_ij != 0, and i=i) */
+  int64_t n_edges;        /* pairs i < j in the pattern                            */
+  int32_t n_offsets;      /* K: distinct column offsets j - i (odd, contains 0)    */
+  int32_t max_offset;     /* largest |j - i|                                       */
+  int64_t device_bytes;   /* device memory held by the problem                     */
+  int32_t assembled;      /* 1 after afc_assemble                                  */
+  int32_t family;         /* afc_family of the assembly                            */
+} afc_info;
+
+/* Options of afc_step / afc_solve_stationary (see afc_default_opts). */
+typedef struct {
+  int32_t scheme;         /* afc_scheme (afc_step only)                                   */
+  int32_t limiter;        /* afc_limiter                                                  */
+  double dt;              /* time step (afc_step); see afc_cfl_timestep                   */
+  double fp_tol;          /* nonlinear stop: ||res||_2 < sqrt(N) * fp_tol (Eq. tol_formula)*/
+  int32_t fp_maxit;       /* max fixed-point iterations                                   */
+  int32_t fp_fixed_its;   /* > 0: run exactly this many fixed-point corrections           */
+  double omega;           /* damping of the fixed point (Sec. 4)                          */
+  int32_t ksp;            /* afc_ksp                                                      */
+  int32_t ksp_maxit;      /* max inner iterations (per solve)                             */
+  double ksp_atol;        /* inner stop: ||r||_2 < max(ksp_atol, ksp_rtol * ||r_0||_2)    */
+  double ksp_rtol;
+  int32_t gmres_restart;  /* GMRES(m) restart length, 1..64                               */
+  int32_t precision;      /* afc_precision: AFC_MIXED runs the inner solve in FP32        */
+  int32_t prelimit;       /* CN: apply Eq. prelimiting (L = 2)                            */
+} afc_opts;
+
+typedef struct {
+  int32_t outer_its;      /* fixed-point corrections (linear solves) performed            */
+  int32_t inner_its;      /* Krylov iterations summed over the solves                     */
+  int32_t stages;         /* explicit FE stages performed                                 */
+  int32_t status;         /* same as the call's return value                              */
+  double res0;            /* first nonlinear residual norm                                */
+  double res_final;       /* last nonlinear residual norm                                 */
+  double umin, umax;      /* extremes of the returned solution                            */
+} afc_stats;
+
+/* ---- lifetime -------------------------------------------------------------- */
+
+/* Uniform box grid [lo, hi] with nx*ny*nz nodes (each >= 2).  P1 cuts every
+ * cell into the six Kuhn tetrahedra sharing the cell diagonal from its corner
+ * (0,0,0) to (1,1,1); Q1 uses one trilinear hexahedron per cell.  `stream` is a
+ * cudaStream_t (or NULL).  On success *out owns the problem. */
+int afc_create_structured(int elem, int nx, int ny, int nz, const double lo[3], const double hi[3],
+                          int device, void* stream, afc_problem* out);
+
+/* Mesh from an element list (host arrays): xyz[3*n_nodes] (x, y, z per node),
+ * conn[4*n_cells] (P1) or conn[8*n_cells] (Q1, local vertex k = dx + 2dy + 4dz
+ * of a box-shaped cell).  The pattern may use at most 63 distinct column
+ * offsets j - i (always true for meshes of up to 32 nodes and for structured
+ * grids); AFC_E_INVALID otherwise. */
+int afc_create_from_elements(int elem, int64_t n_nodes, const double* xyz, int64_t n_cells,
+                             const int32_t* conn, int device, void* stream, afc_problem* out);
+
+int afc_destroy(afc_problem p);
+
+/* ---- data --------------------------------------------------------------------- */
+
+/* Coefficients of Eq. tcdr / Eq. cdr: diffusion eps >= 0, nodal velocity
+ * b_nodal[3*N] (interpolated with the element basis), constant reaction c >= 0,
+ * nodal source f_nodal[N] (NULL = 0).  The load vector is M_L f_nodal. */
+int afc_set_coefficients(afc_problem p, double eps, const double* b_nodal, double c, const double* f_nodal);
+
+/* Dirichlet set: mask[N] (nonzero = Dirichlet node), values[N] (used where mask). */
+int afc_set_dirichlet(afc_problem p, const uint8_t* mask, const double* values);
+
+/* Assemble on the device: M_C, M_L, S, K, A, D and AA (Sec. 2, Eq. low_order_disc)
+ * for the given family; with precision AFC_MIXED also FP32 copies of the system
+ * matrices.  Needs coefficients; Dirichlet data may be set before or after. */
+int afc_assemble(afc_problem p, int family, int precision);
+
+int afc_get_info(afc_problem p, afc_info* out);
+
+/* Copy one matrix out as CSR with sorted columns (host arrays of n_nodes + 1,
+ * nnz, nnz entries; see afc_get_info).  For tests and inspection. */
+int afc_export_csr(afc_problem p, int which, int32_t* rowptr, int32_t* col, double* val);
+
+/* Lumped mass m_i = sum_j m_ij (host array of N). */
+int afc_export_lumped_mass(afc_problem p, double* mL);
+
+/* Solution vector u (N doubles); is_device selects a device or a host pointer. */
+int afc_set_solution(afc_problem p, const double* u, int is_device);
+int afc_get_solution(afc_problem p, double* u, int is_device);
+
+/* Reading of a CFL number: dt = cfl * min over non-Dirichlet i of m_i / AA_ii. */
+int afc_cfl_timestep(afc_problem p, double cfl, double* dt);
+
+void afc_default_opts(afc_opts* o);
+
+/* ---- the hot path ---------------------------------------------------------- */
+
+/* One time step of the stored solution.
+ *  AFC_SSP2 / AFC_SSP3: explicit FE-SSP stages (Eq. FE-SSP) with the predictor
+ *    u~ = u + dt M_L^{-1}(f - AA u) and Zalesak's limiter (Sec. 2.1.2, 2.1.3),
+ *    combined as Heun (SSP2, Sec. 2.1.2) or three-stage Shu-Osher (SSP3).
+ *  AFC_CN_NONLINEAR: Eq. CNZal solved by the damped fixed point of Sec. 4 with
+ *    fluxes Eq. flux_002 (+ Eq. prelimiting if opts->prelimit), the predictor
+ *    Eq. forward_euler and a Jacobi-preconditioned Krylov solve per iteration.
+ * Returns AFC_NOT_CONVERGED (solution updated with the last iterate) if the
+ * fixed point did not reach fp_tol within fp_maxit. */
+int afc_step(afc_problem p, const afc_opts* o, afc_stats* st);
+
+/* Stationary AFC system AA u = f + F*(u) (Sec. 3, Sec. 3.1) with the MC limiter
+ * (Eq. MClimiter) or alpha = 1 / alpha = 0, by the damped fixed point of Sec. 4
+ * in defect form, starting from the stored solution. */
+int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* st);
+
+/* ---- single passes, for parity checks and diagnostics (host arrays) -------- */
+
+/* One forward-Euler FCT stage from the stored solution, without changing it:
+ * predictor u_tilde, Zalesak factors R+ / R-, limited sum F* and the new state
+ * (Eq. FE-SSP).  Any output pointer may be NULL. */
+int afc_fe_stage(afc_problem p, double dt, int limiter, double* u_tilde, double* Rp, double* Rm,
+                 double* Fstar, double* u_new);
+
+/* Limited antidiffusive sum of the CN scheme for given u_new, u_old (host, N):
+ * F*(u_new, u_old) of Eq. CNZal with Zalesak factors built from the CN predictor
+ * of u_old.  Also returns the predictor and R+ / R- (may be NULL). */
+int afc_cn_limited_sum(afc_problem p, double dt, int limiter, int prelimit, const double* u_new,
+                       const double* u_old, double* u_tilde, double* Rp, double* Rm, double* Fstar);
+
+/* MC limited sum F*_i = sum_j r*_ij for a given u (host, N), with the bounds
+ * u_max / u_min of Eq. u_max_min (outputs may be NULL). */
+int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax, double* umin,
+                       double* Fstar);
+
+/* y = AA x (which = AFC_MAT_LOW) or y = M x (AFC_MAT_MC), host arrays of N. */
+int afc_apply(afc_problem p, int which, const double* x, double* y);
+
+/* Solve the system matrix of the stationary problem (system = 0: AA with
+ * identity Dirichlet rows) or of the CN step (system = 1: M_L/dt + AA/2 with
+ * identity Dirichlet rows) for host rhs / x (x in: ignored, out: solution),
+ * Jacobi-preconditioned BiCGStab or GMRES per the options. */
+int afc_linear_solve(afc_problem p, int system, double dt, const afc_opts* o, const double* rhs,
+                     double* x, int* its, double* res);
+
+const char* afc_status_str(int status);
+const char* afc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFC_H */

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of libafc (include/afc.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library.  The
+functions keep the C names; ``Problem`` wraps a handle for convenience.  Arrays
+are numpy float64 (host) or torch CUDA tensors (device, where a call accepts
+device pointers).  Importing this module without a built libafc.so raises
+ImportError: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libafc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "afc.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libafc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+_lib = C.CDLL(LIB_PATH)
+
+# ---- enums (mirror include/afc.h) ----
+AFC_OK, AFC_NOT_CONVERGED = 0, 1
+AFC_E_INVALID, AFC_E_OOM, AFC_E_CUDA, AFC_E_NAN, AFC_E_TIMEOUT, AFC_E_STATE = -1, -2, -3, -4, -5, -6
+AFC_P1, AFC_Q1 = 0, 1
+AFC_FAMILY_FCT, AFC_FAMILY_MC = 0, 1
+AFC_SSP2, AFC_SSP3, AFC_CN_NONLINEAR = 0, 1, 2
+AFC_LIM_NONE, AFC_LIM_GALERKIN, AFC_LIM_ZALESAK, AFC_LIM_MC = 0, 1, 2, 3
+AFC_KSP_BICGSTAB, AFC_KSP_GMRES = 0, 1
+AFC_FP64, AFC_MIXED = 0, 1
+AFC_MAT_MC, AFC_MAT_A, AFC_MAT_D, AFC_MAT_LOW, AFC_MAT_K, AFC_MAT_S = 0, 1, 2, 3, 4, 5
+
+ELEM = {"p1": AFC_P1, "q1": AFC_Q1}
+
+
+class afc_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("nnz", C.c_int64), ("n_edges", C.c_int64), ("n_offsets", C.c_int32),
+                ("max_offset", C.c_int32), ("device_bytes", C.c_int64), ("assembled", C.c_int32),
+                ("family", C.c_int32)]
+
+
+class afc_opts(C.Structure):
+    _fields_ = [("scheme", C.c_int32), ("limiter", C.c_int32), ("dt", C.c_double), ("fp_tol", C.c_double),
+                ("fp_maxit", C.c_int32), ("fp_fixed_its", C.c_int32), ("omega", C.c_double), ("ksp", C.c_int32),
+                ("ksp_maxit", C.c_int32), ("ksp_atol", C.c_double), ("ksp_rtol", C.c_double),
+                ("gmres_restart", C.c_int32), ("precision", C.c_int32), ("prelimit", C.c_int32)]
+
+
+class afc_stats(C.Structure):
+    _fields_ = [("outer_its", C.c_int32), ("inner_its", C.c_int32), ("stages", C.c_int32), ("status", C.c_int32),
+                ("res0", C.c_double), ("res_final", C.c_double), ("umin", C.c_double), ("umax", C.c_double)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_U8 = C.POINTER(C.c_uint8)
+
+_SIGS = {
+    "afc_create_structured": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, _P, C.POINTER(_P)]),
+    "afc_create_from_elements": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, C.c_int, _P, C.POINTER(_P)]),
+    "afc_destroy": (C.c_int, [_P]),
+    "afc_set_coefficients": (C.c_int, [_P, C.c_double, _D, C.c_double, _D]),
+    "afc_set_dirichlet": (C.c_int, [_P, _U8, _D]),
+    "afc_assemble": (C.c_int, [_P, C.c_int, C.c_int]),
+    "afc_get_info": (C.c_int, [_P, C.POINTER(afc_info)]),
+    "afc_export_csr": (C.c_int, [_P, C.c_int, _I32, _I32, _D]),
+    "afc_export_lumped_mass": (C.c_int, [_P, _D]),
+    "afc_set_solution": (C.c_int, [_P, _P, C.c_int]),
+    "afc_get_solution": (C.c_int, [_P, _P, C.c_int]),
+    "afc_cfl_timestep": (C.c_int, [_P, C.c_double, _D]),
+    "afc_default_opts": (None, [C.POINTER(afc_opts)]),
+    "afc_step": (C.c_int, [_P, C.POINTER(afc_opts), C.POINTER(afc_stats)]),
+    "afc_solve_stationary": (C.c_int, [_P, C.POINTER(afc_opts), C.POINTER(afc_stats)]),
+    "afc_fe_stage": (C.c_int, [_P, C.c_double, C.c_int, _D, _D, _D, _D, _D]),
+    "afc_cn_limited_sum": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D]),
+    "afc_mc_limited_sum": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
+    "afc_apply": (C.c_int, [_P, C.c_int, _D, _D]),
+    "afc_linear_solve": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(afc_opts), _D, _D, _I32, _D]),
+    "afc_status_str": (C.c_char_p, [C.c_int]),
+    "afc_last_error": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+EXPORTED = tuple(_SIGS)
+
+
+class AfcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.afc_status_str(status).decode()
+        detail = _lib.afc_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}): {detail}")
+        self.status = status
+
+
+def _check(st: int, where: str, allow_not_converged=False) -> int:
+    if st == AFC_OK or (allow_not_converged and st == AFC_NOT_CONVERGED):
+        return st
+    raise AfcError(st, where)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, n=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def default_opts(**kw) -> afc_opts:
+    o = afc_opts()
+    _lib.afc_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def stats_dict(s: afc_stats) -> dict:
+    return {name: getattr(s, name) for name, _ in afc_stats._fields_}
+
+
+def current_stream_handle():
+    """The current torch CUDA stream as a cudaStream_t, or None (legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch absent
+        pass
+    return None
+
+
+class Problem:
+    """Owner of one afc_problem handle."""
+
+    def __init__(self, handle: C.c_void_p, n_nodes: int):
+        self.h = handle
+        self.N = int(n_nodes)
+
+    @classmethod
+    def structured(cls, elem, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), device=0, stream=None):
+        if np.isscalar(n):
+            n = (int(n),) * 3
+        h = C.c_void_p()
+        lo_a, hi_a = _f64(lo, 3), _f64(hi, 3)
+        st = _lib.afc_create_structured(ELEM.get(elem, elem), int(n[0]), int(n[1]), int(n[2]), _dp(lo_a), _dp(hi_a),
+                                        device, stream if stream is not None else current_stream_handle(),
+                                        C.byref(h))
+        _check(st, "afc_create_structured")
+        return cls(h, int(np.prod(n)))
+
+    @classmethod
+    def from_elements(cls, elem, xyz, conn, device=0, stream=None):
+        xyz = _f64(xyz)
+        conn = np.ascontiguousarray(np.asarray(conn, dtype=np.int32))
+        nl = 4 if ELEM.get(elem, elem) == AFC_P1 else 8
+        h = C.c_void_p()
+        st = _lib.afc_create_from_elements(ELEM.get(elem, elem), xyz.size // 3, _dp(xyz), conn.size // nl,
+                                           conn.ctypes.data_as(_I32), device,
+                                           stream if stream is not None else current_stream_handle(), C.byref(h))
+        _check(st, "afc_create_from_elements")
+        return cls(h, xyz.size // 3)
+
+    def close(self):
+        if self.h:
+            _lib.afc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- data ----
+    def set_coefficients(self, eps, b, c=0.0, f=None):
+        b = _f64(np.broadcast_to(np.asarray(b, dtype=np.float64), (self.N, 3)), 3 * self.N)
+        fa = None if f is None else _f64(np.broadcast_to(np.asarray(f, dtype=np.float64), (self.N,)), self.N)
+        _check(_lib.afc_set_coefficients(self.h, float(eps), _dp(b), float(c), None if fa is None else _dp(fa)),
+               "afc_set_coefficients")
+
+    def set_dirichlet(self, mask, values):
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        v = _f64(np.broadcast_to(np.asarray(values, dtype=np.float64), (self.N,)), self.N)
+        _check(_lib.afc_set_dirichlet(self.h, m.ctypes.data_as(_U8), _dp(v)), "afc_set_dirichlet")
+
+    def assemble(self, family=AFC_FAMILY_FCT, precision=AFC_FP64):
+        _check(_lib.afc_assemble(self.h, family, precision), "afc_assemble")
+
+    def info(self) -> dict:
+        i = afc_info()
+        _check(_lib.afc_get_info(self.h, C.byref(i)), "afc_get_info")
+        return {name: getattr(i, name) for name, _ in afc_info._fields_}
+
+    def export_csr(self, which):
+        inf = self.info()
+        rowptr = np.zeros(self.N + 1, np.int32)
+        col = np.zeros(inf["nnz"], np.int32)
+        val = np.zeros(inf["nnz"], np.float64)
+        _check(_lib.afc_export_csr(self.h, which, rowptr.ctypes.data_as(_I32), col.ctypes.data_as(_I32), _dp(val)),
+               "afc_export_csr")
+        return rowptr, col, val
+
+    def lumped_mass(self):
+        out = np.zeros(self.N)
+        _check(_lib.afc_export_lumped_mass(self.h, _dp(out)), "afc_export_lumped_mass")
+        return out
+
+    def set_solution(self, u):
+        if hasattr(u, "is_cuda") and u.is_cuda:
+            t = u.contiguous().to(dtype=__import__("torch").float64)
+            _check(_lib.afc_set_solution(self.h, C.c_void_p(t.data_ptr()), 1), "afc_set_solution")
+            return
+        a = _f64(u, self.N)
+        _check(_lib.afc_set_solution(self.h, a.ctypes.data_as(C.c_void_p), 0), "afc_set_solution")
+
+    def get_solution(self, out=None):
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            _check(_lib.afc_get_solution(self.h, C.c_void_p(out.data_ptr()), 1), "afc_get_solution")
+            return out
+        a = np.zeros(self.N)
+        _check(_lib.afc_get_solution(self.h, a.ctypes.data_as(C.c_void_p), 0), "afc_get_solution")
+        return a
+
+    def cfl_timestep(self, cfl) -> float:
+        dt = C.c_double()
+        _check(_lib.afc_cfl_timestep(self.h, float(cfl), C.byref(dt)), "afc_cfl_timestep")
+        return dt.value
+
+    # ---- hot path ----
+    def step(self, opts: afc_opts) -> dict:
+        s = afc_stats()
+        st = _lib.afc_step(self.h, C.byref(opts), C.byref(s))
+        _check(st, "afc_step", allow_not_converged=True)
+        return stats_dict(s)
+
+    def solve_stationary(self, opts: afc_opts) -> dict:
+        s = afc_stats()
+        st = _lib.afc_solve_stationary(self.h, C.byref(opts), C.byref(s))
+        _check(st, "afc_solve_stationary", allow_not_converged=True)
+        return stats_dict(s)
+
+    # ---- single passes ----
+    def fe_stage(self, dt, limiter=AFC_LIM_ZALESAK) -> dict:
+        out = {k: np.zeros(self.N) for k in ("u_tilde", "Rp", "Rm", "Fstar", "u_new")}
+        _check(_lib.afc_fe_stage(self.h, float(dt), limiter, *(_dp(out[k]) for k in
+                                 ("u_tilde", "Rp", "Rm", "Fstar", "u_new"))), "afc_fe_stage")
+        return out
+
+    def cn_limited_sum(self, dt, u_new, u_old, limiter=AFC_LIM_ZALESAK, prelimit=1) -> dict:
+        un, uo = _f64(u_new, self.N), _f64(u_old, self.N)
+        out = {k: np.zeros(self.N) for k in ("u_tilde", "Rp", "Rm", "Fstar")}
+        _check(_lib.afc_cn_limited_sum(self.h, float(dt), limiter, prelimit, _dp(un), _dp(uo),
+                                       *(_dp(out[k]) for k in ("u_tilde", "Rp", "Rm", "Fstar"))),
+               "afc_cn_limited_sum")
+        return out
+
+    def mc_limited_sum(self, u, limiter=AFC_LIM_MC) -> dict:
+        ua = _f64(u, self.N)
+        out = {k: np.zeros(self.N) for k in ("umax", "umin", "Fstar")}
+        _check(_lib.afc_mc_limited_sum(self.h, limiter, _dp(ua), *(_dp(out[k]) for k in ("umax", "umin", "Fstar"))),
+               "afc_mc_limited_sum")
+        return out
+
+    def apply(self, which, x):
+        xa = _f64(x, self.N)
+        y = np.zeros(self.N)
+        _check(_lib.afc_apply(self.h, which, _dp(xa), _dp(y)), "afc_apply")
+        return y
+
+    def linear_solve(self, system, rhs, opts: afc_opts, dt=0.0):
+        r = _f64(rhs, self.N)
+        x = np.zeros(self.N)
+        its = C.c_int32()
+        res = C.c_double()
+        st = _lib.afc_linear_solve(self.h, system, float(dt), C.byref(opts), _dp(r), _dp(x), C.byref(its),
+                                   C.byref(res))
+        _check(st, "afc_linear_solve", allow_not_converged=True)
+        return x, its.value, res.value

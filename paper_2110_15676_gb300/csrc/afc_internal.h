@@ -1,0 +1,151 @@
+// Internal declarations of libafc (not part of the C ABI).
+//
+// Storage: every matrix lives in diagonal-offset form ("DIA").  The pattern of
+// a mesh (pairs i, j with m_ij != 0) is described by K distinct column offsets
+// o_0 < ... < o_{K-1} (o = j - i; symmetric set, o_{Kup} = 0).  A full matrix X
+// is stored row-indexed, offset-major: X[k * N + i] = x_{i, i + o_k} (0 where the
+// pair is not in the pattern).  A symmetric edge quantity (m_ij, d_ij) is stored
+// once per pair i < j in the upper half: E[k * N + i] = e_{i, i + o_{Kup+1+k}},
+// k = 0..Kup-1.  Consecutive threads (rows) read consecutive addresses for every
+// k, with no column-index traffic.  Node vectors carry a zero halo of `pad`
+// entries on both sides so that i + o_k is always a valid address.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/afc.h"
+
+namespace afc {
+
+constexpr int kMaxOffsets = 63;       // K <= 63 so that a row's presence mask fits 64 bits
+constexpr int kBlock = 256;           // threads per block of the row kernels
+constexpr int kRedBlocks = 1216;      // blocks of the reduction kernels (8 x 152 SMs)
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define AFC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return afc::cuda_fail(e__, #call); \
+  } while (0)
+
+// Offsets passed by value to kernels (constant bank, unrolled loops).
+struct Offsets {
+  int K;          // number of offsets (odd)
+  int Kup;        // number of positive offsets; index of offset 0 is Kup
+  int o[kMaxOffsets];
+};
+
+// Host-side mesh structure (integer only).
+struct MeshStructure {
+  int elem = 0;                       // AFC_P1 / AFC_Q1
+  int nl = 0;                         // vertices per cell
+  int64_t N = 0, ncells = 0;
+  std::vector<double> xyz;            // 3N
+  std::vector<int32_t> conn;          // nl * ncells
+  std::vector<int32_t> offsets;       // K sorted offsets
+  std::vector<uint64_t> mask;         // N: bit k set iff (i, i + o_k) is in the pattern
+  std::vector<int32_t> inc_ptr;       // N + 1: cells incident to a node
+  std::vector<int32_t> inc;           // (cell << 3) | local vertex
+  int64_t nnz = 0, n_edges = 0;
+};
+
+int build_structured(int elem, int nx, int ny, int nz, const double lo[3], const double hi[3], MeshStructure& m);
+int build_from_elements(int elem, int64_t n_nodes, const double* xyz, int64_t n_cells, const int32_t* conn,
+                        MeshStructure& m);
+
+// Device buffer helpers.
+template <class T>
+struct DBuf {
+  T* base = nullptr;   // allocation
+  T* p = nullptr;      // logical start (after the halo)
+  int64_t n = 0, pad = 0;
+  int alloc(int64_t n_, int64_t pad_ = 0);
+  void free_();
+};
+
+struct KrylovWork;   // defined in krylov.cu
+
+}  // namespace afc
+
+struct afc_problem_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  afc::MeshStructure mesh;
+  afc::Offsets offs{};
+  int64_t N = 0;
+  int K = 0, Kup = 0, pad = 0;
+
+  // mesh on device
+  afc::DBuf<double> xyz;
+  afc::DBuf<int32_t> conn, inc_ptr, inc;
+  afc::DBuf<unsigned long long> mask;
+
+  // coefficients and boundary data
+  bool coef_set = false;
+  double eps = 0.0, c = 0.0;
+  afc::DBuf<double> bnod, fnod;
+  afc::DBuf<uint8_t> dir;
+  afc::DBuf<double> udir;
+
+  // matrices (see the storage note at the top)
+  bool assembled = false;
+  int family = 0, precision = 0;
+  afc::DBuf<double> Mfull, Sfull, Kfull, Afull;   // K * N each
+  afc::DBuf<double> AA;                           // K * N, low-order operator
+  afc::DBuf<double> m_up, d_up;                   // Kup * N, symmetric edge data
+  afc::DBuf<double> mL, f;                        // N
+  afc::DBuf<double> Bst;                          // K * N, stationary system (Dirichlet rows = identity)
+  afc::DBuf<float> Bst32;
+  afc::DBuf<double> dinv_st;
+  afc::DBuf<float> dinv_st32;
+  double cn_dt = -1.0;                            // dt the CN system was built for
+  afc::DBuf<double> Bcn;                          // K * N, M_L/dt + AA/2 (Dirichlet rows = identity)
+  afc::DBuf<float> Bcn32;
+  afc::DBuf<double> dinv_cn;
+  afc::DBuf<float> dinv_cn32;
+
+  // state and work vectors (node vectors carry the halo)
+  afc::DBuf<double> u, u0, ustage, udot, ut, Rp, Rm, Fs, Qp, Qm, b0, res, delta, umax, umin, tmp;
+  afc::DBuf<double> scal;           // small device scalars (norms, dt, ...)
+  afc::DBuf<double> part;           // reduction partials
+  double* host_scal = nullptr;      // pinned host mirror of scal
+
+  afc::KrylovWork* kw = nullptr;
+  int64_t device_bytes = 0;
+};
+
+namespace afc {
+
+// ---- assembly (assemble.cu) ----
+int assemble_device(afc_problem_s* p, int family, int precision);
+int build_cn_system(afc_problem_s* p, double dt);
+
+// ---- kernels of the hot path (fct.cu, mc.cu) ----
+// SSP forward-Euler stage: out = a * uA + b * FE(uin) (Eq. FE-SSP with Zalesak).
+int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double a, const double* uA, double b,
+             double* out);
+// CN helpers
+int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
+int cn_limited_residual(afc_problem_s* p, const double* u_new, const double* u_old, double dt, int limiter,
+                        int prelimit, double* res, double* normsq_slot);            // res + ||res||^2
+// MC
+int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot);
+
+// ---- reductions and BLAS-1 (krylov.cu) ----
+int dot_device(afc_problem_s* p, const double* x, const double* y, double* out_slot);
+int krylov_solve(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, int* its,
+                 double* res);
+int dia_spmv(afc_problem_s* p, const double* A, const double* x, double* y);
+int axpy_device(afc_problem_s* p, double a, const double* x, double* y);   // y += a x
+int minmax_device(afc_problem_s* p, const double* x, double* mn, double* mx);
+void krylov_free(afc_problem_s* p);
+
+int64_t grid_for(int64_t n, int block = kBlock);
+
+}  // namespace afc

@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/afc.h declares, and rejects bad arguments before touching a device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "afc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(afc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("afc_create_structured", "afc_create_from_elements", "afc_set_coefficients", "afc_set_dirichlet",
+                 "afc_assemble", "afc_step", "afc_solve_stationary", "afc_destroy", "afc_export_csr"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2110_15676_gb300 import afc
+    lib = C.CDLL(afc.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(afc.EXPORTED) == set(_declared())
+
+
+def test_default_options_and_status_strings():
+    from paper_2110_15676_gb300 import afc
+    o = afc.default_opts()
+    assert o.fp_tol == 1e-10 and o.ksp_atol == 1e-12 and o.gmres_restart == 20 and o.prelimit == 1
+    assert afc.afc_status_str(afc.AFC_OK) == b"ok"
+    assert b"invalid" in afc.afc_status_str(afc.AFC_E_INVALID)
+
+
+def test_invalid_meshes_rejected_on_host():
+    from paper_2110_15676_gb300 import afc
+    with pytest.raises(afc.AfcError) as e:
+        afc.Problem.structured("p1", (1, 4, 4))
+    assert e.value.status == afc.AFC_E_INVALID
+    with pytest.raises(afc.AfcError):
+        afc.Problem.structured("q1", 4, lo=(0, 0, 0), hi=(1, 0, 1))
+    # out-of-range connectivity
+    xyz = np.zeros((4, 3))
+    with pytest.raises(afc.AfcError) as e:
+        afc.Problem.from_elements("p1", xyz, np.array([[0, 1, 2, 7]]))
+    assert e.value.status == afc.AFC_E_INVALID
+    # too many distinct column offsets for the diagonal-offset storage
+    rng = np.random.default_rng(0)
+    n = 200
+    conn = np.stack([rng.choice(n, 4, replace=False) for _ in range(60)])
+    with pytest.raises(afc.AfcError) as e:
+        afc.Problem.from_elements("p1", rng.uniform(size=(n, 3)), conn)
+    assert "offsets" in str(e.value)
