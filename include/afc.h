@@ -205,6 +205,21 @@ int afc_apply(afc_problem p, int which, const double* x, double* y);
 int afc_linear_solve(afc_problem p, int system, double dt, const afc_opts* o, const double* rhs,
                      double* x, int* its, double* res);
 
+/* ---- diagnostics -------------------------------------------------------------- */
+
+/* Per-kernel device time of the library's launches on this problem.
+ * mode != 0 clears earlier records and starts recording; 0 stops.  While on,
+ * every launch is bracketed by two events on the problem's stream. */
+int afc_profile(afc_problem p, int mode);
+
+/* Recorded totals, one entry per kernel name (at most cap): names[48*k] holds a
+ * NUL-terminated name, total_ms[k] the summed device time, launches[k] the
+ * count; *n receives the number of entries.  *all_launches (may be NULL)
+ * receives the number of kernel launches issued on this problem since its
+ * creation, recorded or not.  Synchronises the stream. */
+int afc_profile_read(afc_problem p, int cap, char* names, double* total_ms, int64_t* launches, int* n,
+                     int64_t* all_launches);
+
 const char* afc_status_str(int status);
 const char* afc_last_error(void);
 

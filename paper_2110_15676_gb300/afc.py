@@ -79,6 +79,9 @@ _SIGS = {
     "afc_mc_limited_sum": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
     "afc_apply": (C.c_int, [_P, C.c_int, _D, _D]),
     "afc_linear_solve": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(afc_opts), _D, _D, _I32, _D]),
+    "afc_profile": (C.c_int, [_P, C.c_int]),
+    "afc_profile_read": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int64)]),
     "afc_status_str": (C.c_char_p, [C.c_int]),
     "afc_last_error": (C.c_char_p, []),
 }
@@ -284,6 +287,31 @@ class Problem:
         y = np.zeros(self.N)
         _check(_lib.afc_apply(self.h, which, _dp(xa), _dp(y)), "afc_apply")
         return y
+
+    def profile(self, on: bool):
+        _check(_lib.afc_profile(self.h, 1 if on else 0), "afc_profile")
+
+    def profile_read(self) -> tuple[dict, int]:
+        """({kernel name: (total_ms, launches)}, launches issued since creation)."""
+        cap = 256
+        names = C.create_string_buffer(48 * cap)
+        tot = np.zeros(cap)
+        cnt = np.zeros(cap, np.int64)
+        n = C.c_int()
+        allc = C.c_int64()
+        _check(_lib.afc_profile_read(self.h, cap, names, _dp(tot), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     C.byref(n), C.byref(allc)), "afc_profile_read")
+        raw = names.raw
+        out = {}
+        for k in range(n.value):
+            nm = raw[48 * k:48 * k + 48].split(b"\0", 1)[0].decode()
+            out[nm] = (float(tot[k]), int(cnt[k]))
+        return out, allc.value
+
+    def launches(self) -> int:
+        allc = C.c_int64()
+        _check(_lib.afc_profile_read(self.h, 0, None, None, None, None, C.byref(allc)), "afc_profile_read")
+        return allc.value
 
     def linear_solve(self, system, rhs, opts: afc_opts, dt=0.0):
         r = _f64(rhs, self.N)

@@ -70,6 +70,26 @@ struct DBuf {
 };
 
 struct KrylovWork;   // defined in krylov.cu
+struct Profiler;     // defined in prof.cpp
+
+}  // namespace afc
+
+struct afc_problem_s;
+
+namespace afc {
+
+// Kernel launches of the library go through AFC_LAUNCH: it counts launches and,
+// while profiling is on, brackets each launch with two events on the stream.
+cudaEvent_t prof_start(afc_problem_s* p);
+void prof_stop(afc_problem_s* p, const char* name, cudaEvent_t start);
+void prof_free(afc_problem_s* p);
+
+#define AFC_LAUNCH(p, name, ...)                       \
+  do {                                                 \
+    cudaEvent_t ev0__ = afc::prof_start(p);            \
+    __VA_ARGS__;                                       \
+    afc::prof_stop(p, name, ev0__);                    \
+  } while (0)
 
 }  // namespace afc
 
@@ -117,6 +137,8 @@ struct afc_problem_s {
   double* host_scal = nullptr;      // pinned host mirror of scal
 
   afc::KrylovWork* kw = nullptr;
+  afc::Profiler* prof = nullptr;
+  int64_t launches = 0;             // kernel launches issued on this problem
   int64_t device_bytes = 0;
 };
 

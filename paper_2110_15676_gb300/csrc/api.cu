@@ -101,6 +101,7 @@ void destroy_all(afc_problem_s* p) {
   if (!p) return;
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  prof_free(p);
   krylov_free(p);
   DBuf<double>* dv[] = {&p->xyz, &p->bnod, &p->fnod, &p->udir, &p->Mfull, &p->Sfull, &p->Kfull, &p->Afull,
                         &p->AA, &p->m_up, &p->d_up, &p->mL, &p->f, &p->Bst, &p->dinv_st, &p->Bcn, &p->dinv_cn,
@@ -396,7 +397,7 @@ int afc_cfl_timestep(afc_problem p, double cfl, double* dt) {
   int st = check(p, true);
   if (st) return st;
   if (!dt || !(cfl > 0.0)) { set_error("need cfl > 0"); return AFC_E_INVALID; }
-  k_cfl_ratio<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->offs, p->AA.p, p->mL.p, p->dir.p, p->tmp.p);
+  AFC_LAUNCH(p, "k_cfl_ratio", k_cfl_ratio<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->offs, p->AA.p, p->mL.p, p->dir.p, p->tmp.p));
   AFC_CUDA(cudaGetLastError());
   double mn, mx;
   if ((st = minmax_device(p, p->tmp.p, &mn, &mx))) return st;
@@ -435,7 +436,7 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   if (p->family != AFC_FAMILY_FCT) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
   if ((st = build_cn_system(p, o->dt))) return st;
   if ((st = cn_predictor(p, p->u0.p, o->dt))) return st;
-  k_apply_dirichlet<<<grid_for(N), kBlock, 0, s>>>(N, p->dir.p, p->udir.p, p->u.p);
+  AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(N), kBlock, 0, s>>>(N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
   const double dt = o->dt;
   st = fixed_point(p, o, 1, stt, [&]() {
@@ -456,7 +457,7 @@ int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
     return AFC_E_INVALID;
   }
   if (lim == AFC_LIM_MC && p->family != AFC_FAMILY_MC) { set_error("MC limiter needs the MC family"); return AFC_E_STATE; }
-  k_apply_dirichlet<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->dir.p, p->udir.p, p->u.p);
+  AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
   st = fixed_point(p, o, 0, stt, [&]() { return mc_limited_residual(p, p->u.p, lim, p->res.p, p->scal.p); });
   if (st < 0) return st;

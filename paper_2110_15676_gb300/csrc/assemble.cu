@@ -240,26 +240,26 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
     return st;
   const int64_t g = grid_for(N);
   if (p->mesh.nl == 4)
-    k_assemble_rows<4><<<g, kBlock, 0, s>>>(N, p->offs, p->xyz.p, p->bnod.p, p->conn.p, p->inc_ptr.p, p->inc.p,
-                                             p->Mfull.p, p->Sfull.p, p->Kfull.p);
+    AFC_LAUNCH(p, "k_assemble_rows", k_assemble_rows<4><<<g, kBlock, 0, s>>>(N, p->offs, p->xyz.p, p->bnod.p, p->conn.p, p->inc_ptr.p, p->inc.p,
+                                             p->Mfull.p, p->Sfull.p, p->Kfull.p));
   else
-    k_assemble_rows<8><<<grid_for(N, 128), 128, 0, s>>>(N, p->offs, p->xyz.p, p->bnod.p, p->conn.p, p->inc_ptr.p,
-                                                         p->inc.p, p->Mfull.p, p->Sfull.p, p->Kfull.p);
+    AFC_LAUNCH(p, "k_assemble_rows", k_assemble_rows<8><<<grid_for(N, 128), 128, 0, s>>>(N, p->offs, p->xyz.p, p->bnod.p, p->conn.p, p->inc_ptr.p,
+                                                         p->inc.p, p->Mfull.p, p->Sfull.p, p->Kfull.p));
   AFC_CUDA(cudaGetLastError());
-  k_lumped_and_A<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->Mfull.p, p->Sfull.p, p->Kfull.p, p->fnod.p,
-                                      p->mL.p, p->f.p, p->Afull.p);
-  k_upwind_edges<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->Afull.p, p->d_up.p);
-  k_low_order<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->mask.p, p->Afull.p, p->Sfull.p, p->mL.p,
-                                   p->d_up.p, p->AA.p);
+  AFC_LAUNCH(p, "k_lumped_and_A", k_lumped_and_A<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->Mfull.p, p->Sfull.p, p->Kfull.p, p->fnod.p,
+                                      p->mL.p, p->f.p, p->Afull.p));
+  AFC_LAUNCH(p, "k_upwind_edges", k_upwind_edges<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->Afull.p, p->d_up.p));
+  AFC_LAUNCH(p, "k_low_order", k_low_order<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->mask.p, p->Afull.p, p->Sfull.p, p->mL.p,
+                                   p->d_up.p, p->AA.p));
   // symmetric mass data of the upper half: m_up[ku][i] = m_{i, i + o}
   for (int ku = 0; ku < Kup; ++ku)
     AFC_CUDA(cudaMemcpyAsync(p->m_up.p + ku * N, p->Mfull.p + (Kup + 1 + ku) * N, N * sizeof(double),
                              cudaMemcpyDeviceToDevice, s));
-  k_system<double><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 1.0, 0.0, p->Bst.p, p->dinv_st.p);
+  AFC_LAUNCH(p, "k_system", k_system<double><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 1.0, 0.0, p->Bst.p, p->dinv_st.p));
   if (precision == AFC_MIXED) {
     if ((st = p->Bst32.alloc(K * N)) || (st = p->dinv_st32.alloc(N, p->pad))) return st;
-    k_system<float><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 1.0, 0.0, p->Bst32.p,
-                                         p->dinv_st32.p);
+    AFC_LAUNCH(p, "k_system", k_system<float><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 1.0, 0.0, p->Bst32.p,
+                                         p->dinv_st32.p));
   }
   AFC_CUDA(cudaGetLastError());
   AFC_CUDA(cudaStreamSynchronize(s));
@@ -276,12 +276,12 @@ int build_cn_system(afc_problem_s* p, double dt) {
   int st;
   if ((st = p->Bcn.alloc(p->K * N)) || (st = p->dinv_cn.alloc(N, p->pad))) return st;
   const int64_t g = grid_for(N);
-  k_system<double><<<g, kBlock, 0, p->stream>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 0.5, dt, p->Bcn.p,
-                                                p->dinv_cn.p);
+  AFC_LAUNCH(p, "k_system", k_system<double><<<g, kBlock, 0, p->stream>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 0.5, dt, p->Bcn.p,
+                                                p->dinv_cn.p));
   if (p->precision == AFC_MIXED) {
     if ((st = p->Bcn32.alloc(p->K * N)) || (st = p->dinv_cn32.alloc(N, p->pad))) return st;
-    k_system<float><<<g, kBlock, 0, p->stream>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 0.5, dt, p->Bcn32.p,
-                                                 p->dinv_cn32.p);
+    AFC_LAUNCH(p, "k_system", k_system<float><<<g, kBlock, 0, p->stream>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 0.5, dt, p->Bcn32.p,
+                                                 p->dinv_cn32.p));
   }
   AFC_CUDA(cudaGetLastError());
   p->cn_dt = dt;

@@ -221,13 +221,13 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
-  k_ssp_rate<<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, uin, p->f.p, p->mL.p, p->dir.p, p->udir.p, dt, p->udot.p,
-                                  p->ut.p);
+  AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, uin, p->f.p, p->mL.p, p->dir.p, p->udir.p, dt, p->udot.p,
+                                  p->ut.p));
   if (limiter == AFC_LIM_ZALESAK)
-    k_ssp_factors<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->m_up.p, p->d_up.p, uin, p->udot.p, p->ut.p, p->mL.p,
-                                       p->dir.p, dt, p->Rp.p, p->Rm.p);
-  k_ssp_correct<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->m_up.p, p->d_up.p, uin, p->udot.p, p->ut.p,
-                                     p->Rp.p, p->Rm.p, p->mL.p, p->dir.p, p->udir.p, dt, a, uA, b, out, p->Fs.p);
+    AFC_LAUNCH(p, "k_ssp_factors", k_ssp_factors<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->m_up.p, p->d_up.p, uin, p->udot.p, p->ut.p, p->mL.p,
+                                       p->dir.p, dt, p->Rp.p, p->Rm.p));
+  AFC_LAUNCH(p, "k_ssp_correct", k_ssp_correct<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->m_up.p, p->d_up.p, uin, p->udot.p, p->ut.p,
+                                     p->Rp.p, p->Rm.p, p->mL.p, p->dir.p, p->udir.p, dt, a, uA, b, out, p->Fs.p));
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
@@ -236,9 +236,9 @@ int cn_predictor(afc_problem_s* p, const double* u_old, double dt) {
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
-  k_cn_predictor<<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, u_old, p->f.p, p->mL.p, p->dir.p, p->udir.p, dt, p->ut.p,
-                                      p->b0.p);
-  k_bounds_of<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->ut.p, p->Qp.p, p->Qm.p);
+  AFC_LAUNCH(p, "k_cn_predictor", k_cn_predictor<<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, u_old, p->f.p, p->mL.p, p->dir.p, p->udir.p, dt, p->ut.p,
+                                      p->b0.p));
+  AFC_LAUNCH(p, "k_bounds_of", k_bounds_of<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->ut.p, p->Qp.p, p->Qm.p));
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
@@ -249,12 +249,12 @@ int cn_limited_residual(afc_problem_s* p, const double* u_new, const double* u_o
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
   if (limiter == AFC_LIM_ZALESAK)
-    k_cn_factors<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->m_up.p, p->d_up.p, u_new, u_old, p->Qp.p, p->Qm.p,
-                                      p->mL.p, p->dir.p, dt, prelimit, p->Rp.p, p->Rm.p);
-  k_cn_residual<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->m_up.p, p->d_up.p, p->AA.p, u_new, u_old,
+    AFC_LAUNCH(p, "k_cn_factors", k_cn_factors<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->m_up.p, p->d_up.p, u_new, u_old, p->Qp.p, p->Qm.p,
+                                      p->mL.p, p->dir.p, dt, prelimit, p->Rp.p, p->Rm.p));
+  AFC_LAUNCH(p, "k_cn_residual", k_cn_residual<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->m_up.p, p->d_up.p, p->AA.p, u_new, u_old,
                                      p->Rp.p, p->Rm.p, p->b0.p, p->mL.p, p->dir.p, dt, prelimit, res, p->Fs.p,
-                                     p->part.p);
-  finalize_sum(p->part.p, (int)g, normsq_slot, s);
+                                     p->part.p));
+  finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }

@@ -78,6 +78,6 @@ __device__ __forceinline__ void block_sums_to(double (&v)[NV], double* part, int
 }
 
 // out[0] = sum of part[0..n) in a fixed order (one block).
-void finalize_sum(const double* part, int n, double* out, cudaStream_t s);
+void finalize_sum(afc_problem_s* p, const double* part, int n, double* out);
 
 }  // namespace afc

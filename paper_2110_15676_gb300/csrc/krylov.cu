@@ -62,7 +62,9 @@ __global__ void k_finalize_sum(const double* __restrict__ part, int n, double* _
 
 }  // namespace
 
-void finalize_sum(const double* part, int n, double* out, cudaStream_t s) { k_finalize_sum<<<1, 1024, 0, s>>>(part, n, out); }
+void finalize_sum(afc_problem_s* p, const double* part, int n, double* out) {
+  AFC_LAUNCH(p, "k_finalize_sum", k_finalize_sum<<<1, 1024, 0, p->stream>>>(part, n, out));
+}
 
 // ---------------------------------------------------------------------------
 // BLAS-1 helpers on double vectors (outer loop)
@@ -128,21 +130,21 @@ __global__ void k_spmv(int64_t N, Offsets of, const T* __restrict__ A, const TV*
 }  // namespace
 
 int dot_device(afc_problem_s* p, const double* x, const double* y, double* out_slot) {
-  k_dot<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, x, y, p->part.p);
-  finalize_sum(p->part.p, kRedBlocks, out_slot, p->stream);
+  AFC_LAUNCH(p, "k_dot", k_dot<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, x, y, p->part.p));
+  finalize_sum(p, p->part.p, kRedBlocks, out_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
 
 int axpy_device(afc_problem_s* p, double a, const double* x, double* y) {
-  k_axpy<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, a, x, y);
+  AFC_LAUNCH(p, "k_axpy", k_axpy<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, a, x, y));
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
 
 int minmax_device(afc_problem_s* p, const double* x, double* mn, double* mx) {
-  k_minmax<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, x, p->part.p);
-  k_minmax_fin<<<1, 32, 0, p->stream>>>(p->part.p, kRedBlocks, p->scal.p + 60);
+  AFC_LAUNCH(p, "k_minmax", k_minmax<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, x, p->part.p));
+  AFC_LAUNCH(p, "k_minmax_fin", k_minmax_fin<<<1, 32, 0, p->stream>>>(p->part.p, kRedBlocks, p->scal.p + 60));
   AFC_CUDA(cudaGetLastError());
   AFC_CUDA(cudaMemcpyAsync(p->host_scal + 60, p->scal.p + 60, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   AFC_CUDA(cudaStreamSynchronize(p->stream));
@@ -152,7 +154,7 @@ int minmax_device(afc_problem_s* p, const double* x, double* mn, double* mx) {
 }
 
 int dia_spmv(afc_problem_s* p, const double* A, const double* x, double* y) {
-  k_spmv<double, double><<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->offs, A, x, y);
+  AFC_LAUNCH(p, "k_spmv", k_spmv<double, double><<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->offs, A, x, y));
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
@@ -651,8 +653,8 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
   const int G = kRedBlocks;
   const int64_t gr = grid_for(N);
   const int64_t pst = std::max<int64_t>(G, gr);
-  k_bicg_init<T><<<G, kBlock, 0, s>>>(N, rhs, x, r, rh, pp, v, part);
-  k_bicg_init_fin<<<1, 1024, 0, s>>>(part, G, sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit);
+  AFC_LAUNCH(p, "k_bicg_init", k_bicg_init<T><<<G, kBlock, 0, s>>>(N, rhs, x, r, rh, pp, v, part));
+  AFC_LAUNCH(p, "k_bicg_init_fin", k_bicg_init_fin<<<1, 1024, 0, s>>>(part, G, sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
   AFC_CUDA(cudaGetLastError());
   int chunk = 2;
   int launched = 0;
@@ -661,21 +663,21 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
     AFC_CUDA(cudaStreamSynchronize(s));
     if (w.hsc[S_DONE] != 0.0 || launched >= o->ksp_maxit) break;
     for (int c = 0; c < chunk && launched < o->ksp_maxit; ++c, ++launched) {
-      k_bicg_p<T><<<G, kBlock, 0, s>>>(N, sc, r, pp, v, dinv, ph);
-      k_bicg_spmv<T, 1><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, ph, v, rh, part, pst);
-      k_bicg_fin_alpha<<<1, 1024, 0, s>>>(part, (int)gr, sc);
-      k_bicg_s<T><<<G, kBlock, 0, s>>>(N, sc, r, v, dinv, sv, sh, part);
-      k_bicg_fin_s<<<1, 1024, 0, s>>>(part, G, sc);
-      k_bicg_early_x<T><<<G, kBlock, 0, s>>>(N, sc, x, ph);
-      k_bicg_spmv<T, 2><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, sh, t, sv, part, pst);
-      k_bicg_fin_omega<<<1, 1024, 0, s>>>(part, (int)gr, pst, sc);
-      k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, pst);
-      k_bicg_fin_r<<<1, 1024, 0, s>>>(part, G, pst, sc);
+      AFC_LAUNCH(p, "k_bicg_p", k_bicg_p<T><<<G, kBlock, 0, s>>>(N, sc, r, pp, v, dinv, ph));
+      AFC_LAUNCH(p, "k_bicg_spmv", k_bicg_spmv<T, 1><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, ph, v, rh, part, pst));
+      AFC_LAUNCH(p, "k_bicg_fin_alpha", k_bicg_fin_alpha<<<1, 1024, 0, s>>>(part, (int)gr, sc));
+      AFC_LAUNCH(p, "k_bicg_s", k_bicg_s<T><<<G, kBlock, 0, s>>>(N, sc, r, v, dinv, sv, sh, part));
+      AFC_LAUNCH(p, "k_bicg_fin_s", k_bicg_fin_s<<<1, 1024, 0, s>>>(part, G, sc));
+      AFC_LAUNCH(p, "k_bicg_early_x", k_bicg_early_x<T><<<G, kBlock, 0, s>>>(N, sc, x, ph));
+      AFC_LAUNCH(p, "k_bicg_spmv", k_bicg_spmv<T, 2><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, sh, t, sv, part, pst));
+      AFC_LAUNCH(p, "k_bicg_fin_omega", k_bicg_fin_omega<<<1, 1024, 0, s>>>(part, (int)gr, pst, sc));
+      AFC_LAUNCH(p, "k_bicg_xr", k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, pst));
+      AFC_LAUNCH(p, "k_bicg_fin_r", k_bicg_fin_r<<<1, 1024, 0, s>>>(part, G, pst, sc));
     }
     AFC_CUDA(cudaGetLastError());
     chunk = std::min(chunk * 2, 16);
   }
-  k_to_double<T><<<G, kBlock, 0, s>>>(N, x, xout);
+  AFC_LAUNCH(p, "k_to_double", k_to_double<T><<<G, kBlock, 0, s>>>(N, x, xout));
   AFC_CUDA(cudaGetLastError());
   if (its) *its = (int)w.hsc[S_ITS];
   if (res) *res = w.hsc[S_NRES];
@@ -703,31 +705,31 @@ int gmres_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, c
   const int64_t gr = grid_for(N);
   const int64_t pst = std::max<int64_t>(G, gr);
   AFC_CUDA(cudaMemsetAsync(x - p->pad, 0, vs * sizeof(T), s));
-  k_gm_reset<<<1, 32, 0, s>>>(sc);
+  AFC_LAUNCH(p, "k_gm_reset", k_gm_reset<<<1, 32, 0, s>>>(sc));
   for (;;) {
     // true residual, stop test, new cycle
-    k_gm_residual<T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, x, rhs, wv, part);
-    k_gm_start<<<1, 1024, 0, s>>>(part, (int)gr, sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit);
+    AFC_LAUNCH(p, "k_gm_residual", k_gm_residual<T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, x, rhs, wv, part));
+    AFC_LAUNCH(p, "k_gm_start", k_gm_start<<<1, 1024, 0, s>>>(part, (int)gr, sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
     AFC_CUDA(cudaGetLastError());
     AFC_CUDA(cudaMemcpyAsync(w.hsc, sc, S_CS * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFC_CUDA(cudaStreamSynchronize(s));
     if (w.hsc[S_DONE] != 0.0) break;
-    k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V, dinv, z);
+    AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V, dinv, z));
     for (int k = 0; k < m; ++k) {
-      k_gm_spmv<T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv);
-      k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, -1, wv, V, vs, part, G, 0);
-      k_gm_fin_dots<<<1, 1024, 0, s>>>(part, G, G, k + 1, sc, S_H1);
-      k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, S_H1, wv, V, vs, part, G, 0);
-      k_gm_fin_dots<<<1, 1024, 0, s>>>(part, G, G, k + 1, sc, S_H2);
-      k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, S_H2, wv, V, vs, part, G, 1);
-      k_gm_column<<<1, 1024, 0, s>>>(part, G, sc, k, m);
-      k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z);
+      AFC_LAUNCH(p, "k_gm_spmv", k_gm_spmv<T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv));
+      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, -1, wv, V, vs, part, G, 0));
+      AFC_LAUNCH(p, "k_gm_fin_dots", k_gm_fin_dots<<<1, 1024, 0, s>>>(part, G, G, k + 1, sc, S_H1));
+      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, S_H1, wv, V, vs, part, G, 0));
+      AFC_LAUNCH(p, "k_gm_fin_dots", k_gm_fin_dots<<<1, 1024, 0, s>>>(part, G, G, k + 1, sc, S_H2));
+      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, S_H2, wv, V, vs, part, G, 1));
+      AFC_LAUNCH(p, "k_gm_column", k_gm_column<<<1, 1024, 0, s>>>(part, G, sc, k, m));
+      AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z));
     }
-    k_gm_solve<<<1, 32, 0, s>>>(sc);
-    k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv);
+    AFC_LAUNCH(p, "k_gm_solve", k_gm_solve<<<1, 32, 0, s>>>(sc));
+    AFC_LAUNCH(p, "k_gm_update", k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv));
     AFC_CUDA(cudaGetLastError());
   }
-  k_to_double<T><<<G, kBlock, 0, s>>>(N, x, xout);
+  AFC_LAUNCH(p, "k_to_double", k_to_double<T><<<G, kBlock, 0, s>>>(N, x, xout));
   AFC_CUDA(cudaGetLastError());
   if (its) *its = (int)w.hsc[S_ITS];
   if (res) *res = w.hsc[S_NRES];

@@ -86,10 +86,10 @@ int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* 
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
   if (limiter == AFC_LIM_MC)
-    k_mc_bounds<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, u, p->umax.p, p->umin.p);
-  k_mc_residual<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->d_up.p, p->Kfull.p, p->AA.p, u, p->umax.p,
-                                     p->umin.p, p->f.p, p->dir.p, res, p->Fs.p, p->part.p);
-  finalize_sum(p->part.p, (int)g, normsq_slot, s);
+    AFC_LAUNCH(p, "k_mc_bounds", k_mc_bounds<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, u, p->umax.p, p->umin.p));
+  AFC_LAUNCH(p, "k_mc_residual", k_mc_residual<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->d_up.p, p->Kfull.p, p->AA.p, u, p->umax.p,
+                                     p->umin.p, p->f.p, p->dir.p, res, p->Fs.p, p->part.p));
+  finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
