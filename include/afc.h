@@ -195,6 +195,22 @@ int afc_cn_limited_sum(afc_problem p, double dt, int limiter, int prelimit, cons
 int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax, double* umin,
                        double* Fstar);
 
+/* Same limited sum as afc_mc_limited_sum, for callers that cannot allocate
+ * device memory (for example code running while a stream is being captured, or
+ * an embedding runtime that forbids cudaMalloc after start-up).  The paper has
+ * no counterpart; this is a deployment variant.
+ *  u      device array of N doubles (no halo needed), input state;
+ *  Fstar  device array of N doubles, output F*_i (0 at Dirichlet rows).
+ * The bounds u_max / u_min it needs live in a fixed 4 MiB device array that
+ * every GPU loading the library holds until exit, so N may be at most 262144
+ * (AFC_E_INVALID otherwise).  No cudaMalloc, cudaFree or allocating library
+ * call is made.  Work is enqueued on the problem's stream and the call returns
+ * without synchronising.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams or other problems on the same device) race. */
+int afc_mc_limited_sum_noalloc(afc_problem p, int limiter, const double* u, double* Fstar);
+
 /* y = AA x (which = AFC_MAT_LOW) or y = M x (AFC_MAT_MC), host arrays of N. */
 int afc_apply(afc_problem p, int which, const double* x, double* y);
 

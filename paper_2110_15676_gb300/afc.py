@@ -77,6 +77,7 @@ _SIGS = {
     "afc_fe_stage": (C.c_int, [_P, C.c_double, C.c_int, _D, _D, _D, _D, _D]),
     "afc_cn_limited_sum": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D]),
     "afc_mc_limited_sum": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
+    "afc_mc_limited_sum_noalloc": (C.c_int, [_P, C.c_int, _P, _P]),
     "afc_apply": (C.c_int, [_P, C.c_int, _D, _D]),
     "afc_linear_solve": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(afc_opts), _D, _D, _I32, _D]),
     "afc_profile": (C.c_int, [_P, C.c_int]),
@@ -281,6 +282,12 @@ class Problem:
         _check(_lib.afc_mc_limited_sum(self.h, limiter, _dp(ua), *(_dp(out[k]) for k in ("umax", "umin", "Fstar"))),
                "afc_mc_limited_sum")
         return out
+
+    def mc_limited_sum_noalloc(self, u, Fstar, limiter=AFC_LIM_MC):
+        """Device-pointer variant that allocates nothing (u, Fstar: CUDA float64 tensors of N)."""
+        _check(_lib.afc_mc_limited_sum_noalloc(self.h, limiter, C.c_void_p(u.data_ptr()),
+                                               C.c_void_p(Fstar.data_ptr())), "afc_mc_limited_sum_noalloc")
+        return Fstar
 
     def apply(self, which, x):
         xa = _f64(x, self.N)
