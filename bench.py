@@ -121,17 +121,100 @@ def _opts(afc, dt, mixed=False):
     return afc.default_opts(scheme=afc.AFC_CN_NONLINEAR, dt=dt, fp_tol=FP_TOL, fp_maxit=100, ksp_atol=KSP_ATOL)
 
 
-# Algorithmic work per launch of the kernels that can dominate (stated in the design notes):
-#   FP64 flops: SpMV 2 per pattern entry; BiCGStab fused dots 2 per row.
+# Algorithmic FP64 work per launch of the kernels that can dominate a CN step (the design
+# notes state the counts): SpMV 2 flops per pattern entry, a fused dot 2 per row; the CN
+# flux of Eq. flux_002 with node sums precomputed 5 per pair + 1 for the prelimiter
+# argument; P+/- 1 per directed pair; alpha r_ij accumulated 2 per directed pair.
 def _kernel_work(name, N, nnz, E):
-    if name.startswith("k_bicg_spmv"):
+    if name == "k_bicg_spmv1":
         return ("alu", 2.0 * nnz + 2.0 * N, "TFLOP/s")
+    if name == "k_bicg_spmv2":
+        return ("alu", 2.0 * nnz + 4.0 * N, "TFLOP/s")
     if name == "k_cn_residual":
-        # r_ij (8) + alpha r_ij (1) per directed pair, SpMV 2 per entry
-        return ("alu", 9.0 * 2 * E + 2.0 * nnz, "TFLOP/s")
+        return ("alu", 2.0 * (2 * E) + 2.0 * nnz, "TFLOP/s")
     if name == "k_cn_factors":
-        return ("alu", 9.0 * 2 * E, "TFLOP/s")
+        return ("alu", 1.0 * (2 * E), "TFLOP/s")
+    if name == "k_cn_edges":
+        return ("alu", 6.0 * E, "TFLOP/s")
     return (None, None, None)
+
+
+def _timed_steps(P, opts, steps, flush, stream, torch):
+    """Time `steps` steps one by one with CUDA events on the problem's stream, L2 flushed
+    (not timed) before each.  Returns (ms, fixed-point its, Krylov its, statuses)."""
+    ms_total, its_total, inner_total, statuses = 0.0, 0, 0, []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = P.step(opts)
+        e1.record(stream)
+        e1.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        its_total += st["outer_its"]
+        inner_total += st["inner_its"]
+        statuses.append(st["status"])
+    return ms_total, its_total, inner_total, statuses
+
+
+def _roofline(name, kms, kcount, work_flops, share):
+    achieved = work_flops / (kms / kcount / 1e3) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit counts, max clock)",
+            "avg_launch_us": kms / kcount * 1e3, "share": share}
+
+
+def mc_sweep(afc, W, torch, flush, stream, reps):
+    """The stationary MC limiter + residual sweep on Kuhn P1 129^3 (2,146,689 dofs):
+    bounds, limited fluxes of all 14.8 M pairs, residual SpMV and norm."""
+    wl = W.stationary_inflow("p1", 129)
+    P = afc.Problem.structured(wl.elem, wl.n)
+    P.set_coefficients(wl.eps, wl.b, wl.c, wl.f)
+    P.set_dirichlet(wl.dir_mask, wl.u_dir)
+    P.assemble(afc.AFC_FAMILY_MC, afc.AFC_FP64)
+    rng = np.random.default_rng(3)
+    u = np.where(wl.dir_mask.astype(bool), wl.u_dir, rng.uniform(0.0, 1.0, wl.n_nodes))
+    P.set_solution(u)
+    info = P.info()
+    N, nnz, E = info["n_nodes"], info["nnz"], info["n_edges"]
+    for _ in range(3):
+        P.mc_residual_sweep(afc.AFC_LIM_MC)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.mc_residual_sweep(afc.AFC_LIM_MC)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    P.profile(True)
+    for _ in range(reps):
+        flush.fill_(1.0)
+        P.mc_residual_sweep(afc.AFC_LIM_MC)
+    prof, _ = P.profile_read()
+    P.profile(False)
+    sweep_ms = ms / reps
+    # algorithmic work of one sweep (design notes): FP64 flops 14 per pair + 2 per entry;
+    # bytes of the CSR count 4(N+1) + 12 nnz + 24 E + 24 N
+    flops = 14.0 * E + 2.0 * nnz
+    alg_bytes = 4.0 * (N + 1) + 12.0 * nnz + 24.0 * E + 24.0 * N
+    peaks, src = _peaks()
+    out = {"workload": "stationary MC, Kuhn P1 129^3 (2146689 dofs, 14827904 pairs), eps=1e-8, c=1, b=(1,-0.5,0.25)",
+           "ms_per_sweep": sweep_ms, "dof_sweeps_per_s": N / (sweep_ms / 1e3),
+           "hbm": {"bound": "hbm", "achieved": alg_bytes / (sweep_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                   "unit": "GB/s", "frac": alg_bytes / (sweep_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                   "algorithmic_bytes": alg_bytes, "peak_source": src},
+           "alu": {"bound": "alu", "achieved": flops / (sweep_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                   "unit": "TFLOP/s", "frac": flops / (sweep_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                   "algorithmic_flops": flops},
+           "kernels": {k: {"ms": v[0] / reps, "launches": v[1] // reps} for k, v in prof.items()}}
+    del P
+    return out
 
 
 def run_ours(args, ws, rank, local):
@@ -150,6 +233,7 @@ def run_ours(args, ws, rank, local):
     dt = P.cfl_timestep(CFL)
     opts = _opts(afc, dt)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    stream = torch.cuda.current_stream()
 
     def barrier():
         if ws > 1:
@@ -162,49 +246,28 @@ def run_ours(args, ws, rank, local):
     clocks = ClockSampler(local)
     time.sleep(0.3)
     launches0 = P.launches()
-    P.profile(True)
-    stream = torch.cuda.current_stream()
-    ms_total, its_total, inner_total = 0.0, 0, 0
-    statuses = []
     barrier()
-    for _ in range(args.steps):
-        flush.fill_(1.0)                       # evict L2 between timed steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = P.step(opts)
-        e1.record(stream)
-        e1.synchronize()
-        ms_total += e0.elapsed_time(e1)
-        its_total += st["outer_its"]
-        inner_total += st["inner_its"]
-        statuses.append(st["status"])
+    ms_total, its_total, inner_total, statuses = _timed_steps(P, opts, args.steps, flush, stream, torch)
     barrier()
     clk = clocks.stop()
-    prof, launches1 = P.profile_read()
-    P.profile(False)
-    gpu_launches = launches1 - launches0
+    gpu_launches = P.launches() - launches0
     t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    units = float(N) * its_total * ws
-    value = units / (ms_max / 1e3)
+    value = float(N) * its_total * ws / (ms_max / 1e3)
 
-    # dominant kernel and its roofline
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (kms, kcount) = dom
+    # per-kernel device time: the same steps again with every launch bracketed by events
+    P.profile(True)
+    _timed_steps(P, opts, args.steps, flush, stream, torch)
+    prof, _ = P.profile_read()
+    P.profile(False)
+    tot_ms = sum(v[0] for v in prof.values())
+    name, (kms, kcount) = max(prof.items(), key=lambda kv: kv[1][0])
     bound, work, unit = _kernel_work(name, N, nnz, E)
-    peaks, peak_src = _peaks()
-    roof = None
-    if bound == "alu":
-        achieved = work / (kms / kcount / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": unit,
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe 152 SM x 2 DFMA/clk x 2.07 GHz",
-                "avg_launch_us": kms / kcount * 1e3, "share": kms / sum(v[0] for v in prof.values())}
+    roof = _roofline(name, kms, kcount, work, kms / tot_ms) if bound == "alu" else None
 
-    # mixed precision variant (FP32 inner BiCGStab), same workload, fewer steps
+    # mixed precision variant (FP32 inner BiCGStab), same workload
     mixed = None
     if args.steps > 0:
         Pm, _ = _make_problem(afc, W, afc.AFC_MIXED)
@@ -212,18 +275,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(max(1, args.warmup)):
             Pm.step(om)
         torch.cuda.synchronize()
-        mms, mits = 0.0, 0
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = Pm.step(om)
-            e1.record(stream)
-            e1.synchronize()
-            mms += e0.elapsed_time(e1)
-            mits += st["outer_its"]
-        # accuracy of the mixed result against the FP64 path after the same number of steps
+        mms, mits, _, _ = _timed_steps(Pm, om, args.steps, flush, stream, torch)
         Pr, _ = _make_problem(afc, W, afc.AFC_FP64)
         for _ in range(max(1, args.warmup) + args.steps):
             Pr.step(opts)
@@ -254,6 +306,11 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": float(N) * e2e_its * ws / (float(te.item()) / 1e3), "unit": "dof-iters/s",
            "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
 
+    sweep = None
+    if not args.no_mc_sweep and args.steps > 0:
+        del P
+        sweep = mc_sweep(afc, W, torch, flush, stream, max(args.steps, 5))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_its)
@@ -267,8 +324,10 @@ def run_ours(args, ws, rank, local):
                        "fixed_point_its": its_total, "krylov_its": inner_total,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
-            "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]},
-            "mixed": mixed, "cpu_baseline": cpu,
+            "kernels": {k: {"ms": v[0], "launches": v[1]}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]},
+            "kernel_times": "second pass of the same steps with per-launch CUDA events",
+            "mixed": mixed, "mc_sweep": sweep, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -332,6 +391,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mc-sweep", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=6)
     args = ap.parse_args()
     ws, rank, local = _dist()

@@ -211,6 +211,12 @@ int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax
  * streams or other problems on the same device) race. */
 int afc_mc_limited_sum_noalloc(afc_problem p, int limiter, const double* u, double* Fstar);
 
+/* One limiter + residual sweep of the stationary problem on the stored solution:
+ * bounds (Eq. u_max_min), limited fluxes (Eq. MClimiter, or alpha = 1 / 0 per
+ * `limiter`) and res = f + F*(u) - AA u into internal buffers.  Only enqueued on
+ * the problem's stream (no synchronisation, no host copy): for timing the sweep. */
+int afc_mc_residual_sweep(afc_problem p, int limiter);
+
 /* y = AA x (which = AFC_MAT_LOW) or y = M x (AFC_MAT_MC), host arrays of N. */
 int afc_apply(afc_problem p, int which, const double* x, double* y);
 

@@ -78,6 +78,7 @@ _SIGS = {
     "afc_cn_limited_sum": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D]),
     "afc_mc_limited_sum": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
     "afc_mc_limited_sum_noalloc": (C.c_int, [_P, C.c_int, _P, _P]),
+    "afc_mc_residual_sweep": (C.c_int, [_P, C.c_int]),
     "afc_apply": (C.c_int, [_P, C.c_int, _D, _D]),
     "afc_linear_solve": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(afc_opts), _D, _D, _I32, _D]),
     "afc_profile": (C.c_int, [_P, C.c_int]),
@@ -288,6 +289,10 @@ class Problem:
         _check(_lib.afc_mc_limited_sum_noalloc(self.h, limiter, C.c_void_p(u.data_ptr()),
                                                C.c_void_p(Fstar.data_ptr())), "afc_mc_limited_sum_noalloc")
         return Fstar
+
+    def mc_residual_sweep(self, limiter=AFC_LIM_MC):
+        """Enqueue one MC limiter + residual sweep on the stored solution (no sync)."""
+        _check(_lib.afc_mc_residual_sweep(self.h, limiter), "afc_mc_residual_sweep")
 
     def apply(self, which, x):
         xa = _f64(x, self.N)

@@ -126,12 +126,15 @@ struct afc_problem_s {
   afc::DBuf<float> dinv_st32;
   double cn_dt = -1.0;                            // dt the CN system was built for
   afc::DBuf<double> Bcn;                          // K * N, M_L/dt + AA/2 (Dirichlet rows = identity)
+  afc::DBuf<double> mdt_up;                       // Kup * N, m_ij / dt of the CN step
+  afc::DBuf<double> mLdt;                         // N, m_i / dt
   afc::DBuf<float> Bcn32;
   afc::DBuf<double> dinv_cn;
   afc::DBuf<float> dinv_cn32;
 
   // state and work vectors (node vectors carry the halo)
-  afc::DBuf<double> u, u0, ustage, udot, ut, Rp, Rm, Fs, Qp, Qm, b0, res, delta, umax, umin, tmp;
+  afc::DBuf<double> u, u0, ustage, udot, ut, Rp, Rm, Fs, Qp, Qm, b0, res, delta, umax, umin, tmp, cn_a, cn_s;
+  afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
   afc::DBuf<double> scal;           // small device scalars (norms, dt, ...)
   afc::DBuf<double> part;           // reduction partials
   double* host_scal = nullptr;      // pinned host mirror of scal
@@ -154,8 +157,10 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
              double* out);
 // CN helpers
 int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
-int cn_limited_residual(afc_problem_s* p, const double* u_new, const double* u_old, double dt, int limiter,
-                        int prelimit, double* res, double* normsq_slot);            // res + ||res||^2
+// a = u - u_old, s = u + u_old after u += omega * delta (delta may be null)
+int cn_update(afc_problem_s* p, double omega, const double* delta, double* u, const double* u_old);
+int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int limiter, int prelimit, double* res,
+                        double* normsq_slot);                                      // needs cn_update first
 // MC
 int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot);
 

@@ -79,8 +79,9 @@ int create_common(afc_problem_s* p) {
       (st = p->inc.alloc((int64_t)m.inc.size())) || (st = p->mask.alloc(N)) || (st = p->bnod.alloc(3 * N)) ||
       (st = p->fnod.alloc(N)) || (st = p->dir.alloc(N)) || (st = p->udir.alloc(N)))
     return st;
-  DBuf<double>* vecs[] = {&p->u, &p->u0, &p->ustage, &p->udot, &p->ut, &p->Rp, &p->Rm, &p->Fs,
-                          &p->Qp, &p->Qm, &p->b0, &p->res, &p->delta, &p->umax, &p->umin, &p->tmp};
+  DBuf<double>* vecs[] = {&p->u,  &p->u0,  &p->ustage, &p->udot, &p->ut,   &p->Rp,  &p->Rm,
+                          &p->Fs, &p->Qp,  &p->Qm,     &p->b0,   &p->res,  &p->delta, &p->umax,
+                          &p->umin, &p->tmp, &p->cn_a, &p->cn_s};
   for (auto* v : vecs)
     if ((st = v->alloc(N, p->pad))) return st;
   if ((st = p->scal.alloc(64)) || (st = p->part.alloc(4 * std::max<int64_t>(kRedBlocks, grid_for(N))))) return st;
@@ -106,7 +107,8 @@ void destroy_all(afc_problem_s* p) {
   DBuf<double>* dv[] = {&p->xyz, &p->bnod, &p->fnod, &p->udir, &p->Mfull, &p->Sfull, &p->Kfull, &p->Afull,
                         &p->AA, &p->m_up, &p->d_up, &p->mL, &p->f, &p->Bst, &p->dinv_st, &p->Bcn, &p->dinv_cn,
                         &p->u, &p->u0, &p->ustage, &p->udot, &p->ut, &p->Rp, &p->Rm, &p->Fs, &p->Qp, &p->Qm,
-                        &p->b0, &p->res, &p->delta, &p->umax, &p->umin, &p->tmp, &p->scal, &p->part};
+                        &p->b0, &p->res, &p->delta, &p->umax, &p->umin, &p->tmp, &p->cn_a, &p->cn_s,
+                        &p->scal, &p->part, &p->r_up, &p->mdt_up, &p->mLdt};
   for (auto* b : dv) b->free_();
   p->Bst32.free_(); p->dinv_st32.free_(); p->Bcn32.free_(); p->dinv_cn32.free_();
   p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_();
@@ -127,8 +129,8 @@ int finish_stats(afc_problem_s* p, afc_stats* st, int status) {
 
 // Damped fixed point of Sec. 4 in defect form: res = residual(u); stop if
 // ||res|| < sqrt(N) tol; solve B delta = res; u += omega delta.
-template <class Residual>
-int fixed_point(afc_problem_s* p, const afc_opts* o, int system, afc_stats* st, Residual residual) {
+template <class Residual, class Update>
+int fixed_point(afc_problem_s* p, const afc_opts* o, int system, afc_stats* st, Residual residual, Update update) {
   const double thresh = std::sqrt((double)p->N) * o->fp_tol;
   int status = AFC_NOT_CONVERGED;
   for (int it = 0;; ++it) {
@@ -156,7 +158,7 @@ int fixed_point(afc_problem_s* p, const afc_opts* o, int system, afc_stats* st, 
       st->inner_its += its;
       st->outer_its += 1;
     }
-    if ((e = axpy_device(p, o->omega, p->delta.p, p->u.p))) return e;
+    if ((e = update())) return e;
   }
   return status;
 }
@@ -438,10 +440,11 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   if ((st = cn_predictor(p, p->u0.p, o->dt))) return st;
   AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(N), kBlock, 0, s>>>(N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
+  if ((st = cn_update(p, 0.0, nullptr, p->u.p, p->u0.p))) return st;
   const double dt = o->dt;
-  st = fixed_point(p, o, 1, stt, [&]() {
-    return cn_limited_residual(p, p->u.p, p->u0.p, dt, lim, o->prelimit, p->res.p, p->scal.p);
-  });
+  st = fixed_point(
+      p, o, 1, stt, [&]() { return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, p->scal.p); },
+      [&]() { return cn_update(p, o->omega, p->delta.p, p->u.p, p->u0.p); });
   if (st < 0) return st;
   return finish_stats(p, stt, st);
 }
@@ -459,7 +462,9 @@ int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
   if (lim == AFC_LIM_MC && p->family != AFC_FAMILY_MC) { set_error("MC limiter needs the MC family"); return AFC_E_STATE; }
   AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
-  st = fixed_point(p, o, 0, stt, [&]() { return mc_limited_residual(p, p->u.p, lim, p->res.p, p->scal.p); });
+  st = fixed_point(
+      p, o, 0, stt, [&]() { return mc_limited_residual(p, p->u.p, lim, p->res.p, p->scal.p); },
+      [&]() { return axpy_device(p, o->omega, p->delta.p, p->u.p); });
   if (st < 0) return st;
   return finish_stats(p, stt, st);
 }
@@ -483,8 +488,10 @@ int afc_cn_limited_sum(afc_problem p, double dt, int limiter, int prelimit, cons
   if (st) return st;
   if (!(dt > 0.0) || !u_new || !u_old) { set_error("need dt > 0, u_new, u_old"); return AFC_E_INVALID; }
   if ((st = to_device(p, p->ustage.p, u_new, p->N)) || (st = to_device(p, p->u0.p, u_old, p->N))) return st;
+  if ((st = build_cn_system(p, dt))) return st;
   if ((st = cn_predictor(p, p->u0.p, dt))) return st;
-  if ((st = cn_limited_residual(p, p->ustage.p, p->u0.p, dt, limiter, prelimit, p->res.p, p->scal.p))) return st;
+  if ((st = cn_update(p, 0.0, nullptr, p->ustage.p, p->u0.p))) return st;
+  if ((st = cn_limited_residual(p, p->ustage.p, dt, limiter, prelimit, p->res.p, p->scal.p))) return st;
   if ((st = to_host(p, u_tilde, p->ut.p, p->N)) || (st = to_host(p, Rp, p->Rp.p, p->N)) ||
       (st = to_host(p, Rm, p->Rm.p, p->N)) || (st = to_host(p, Fstar, p->Fs.p, p->N)))
     return st;
@@ -501,6 +508,16 @@ int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax
       (st = to_host(p, Fstar, p->Fs.p, p->N)))
     return st;
   return sync(p);
+}
+
+int afc_mc_residual_sweep(afc_problem p, int limiter) {
+  int st = check(p, true);
+  if (st) return st;
+  if (limiter != AFC_LIM_NONE && limiter != AFC_LIM_GALERKIN && limiter != AFC_LIM_MC) {
+    set_error("limiter must be NONE, GALERKIN or MC");
+    return AFC_E_INVALID;
+  }
+  return mc_limited_residual(p, p->u.p, limiter, p->res.p, p->scal.p);
 }
 
 int afc_apply(afc_problem p, int which, const double* x, double* y) {

@@ -236,7 +236,7 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
   if ((st = p->Mfull.alloc(K * N)) || (st = p->Sfull.alloc(K * N)) || (st = p->Kfull.alloc(K * N)) ||
       (st = p->Afull.alloc(K * N)) || (st = p->AA.alloc(K * N)) || (st = p->m_up.alloc(Kup * N)) ||
       (st = p->d_up.alloc(Kup * N)) || (st = p->mL.alloc(N, p->pad)) || (st = p->f.alloc(N, p->pad)) ||
-      (st = p->Bst.alloc(K * N)) || (st = p->dinv_st.alloc(N, p->pad)))
+      (st = p->Bst.alloc(K * N)) || (st = p->dinv_st.alloc(N, p->pad)) || (st = p->r_up.alloc(Kup * N)))
     return st;
   const int64_t g = grid_for(N);
   if (p->mesh.nl == 4)
@@ -270,12 +270,25 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
   return AFC_OK;
 }
 
+namespace {
+// m_ij / dt for the pairs and m_i / dt for the nodes of the CN step
+__global__ void k_scale_by_dt(int64_t n, const double* __restrict__ x, double dt, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] / dt;
+}
+}  // namespace
+
 int build_cn_system(afc_problem_s* p, double dt) {
   if (p->cn_dt == dt) return AFC_OK;
   const int64_t N = p->N;
   int st;
-  if ((st = p->Bcn.alloc(p->K * N)) || (st = p->dinv_cn.alloc(N, p->pad))) return st;
+  if ((st = p->Bcn.alloc(p->K * N)) || (st = p->dinv_cn.alloc(N, p->pad)) || (st = p->mdt_up.alloc(p->Kup * N)) ||
+      (st = p->mLdt.alloc(N, p->pad)))
+    return st;
   const int64_t g = grid_for(N);
+  AFC_LAUNCH(p, "k_scale_by_dt", k_scale_by_dt<<<grid_for(p->Kup * N), kBlock, 0, p->stream>>>(p->Kup * N, p->m_up.p,
+                                                                                              dt, p->mdt_up.p));
+  AFC_LAUNCH(p, "k_scale_by_dt", k_scale_by_dt<<<g, kBlock, 0, p->stream>>>(N, p->mL.p, dt, p->mLdt.p));
   AFC_LAUNCH(p, "k_system", k_system<double><<<g, kBlock, 0, p->stream>>>(N, p->offs, p->AA.p, p->mL.p, p->dir.p, 0.5, dt, p->Bcn.p,
                                                 p->dinv_cn.p));
   if (p->precision == AFC_MIXED) {

@@ -1,9 +1,15 @@
 // Zalesak flux-corrected transport passes (Sec. 2.1): the explicit FE-SSP stage
 // (Sec. 2.1.2) and the Crank-Nicolson residual (Sec. 2.1.1), both with Zalesak's
-// limiter (Sec. 2.1.3).  One thread owns one row i and visits its neighbours j
-// through the column offsets; the symmetric coefficients m_ij, d_ij of a pair
-// are read from the row of its lower node, so each row sees the same numbers as
-// its partner and r_ji = -r_ij, alpha_ji = alpha_ij hold by construction.
+// limiter (Sec. 2.1.3).
+//
+// Structure.  Each pass of a stage is one kernel over the rows; a pair's flux
+// r_ij is computed once, by the row of its lower node, and stored in r_up (the
+// upper half of the pattern, r_ji = -r_ij).  The node passes that need all
+// fluxes of a row (P+/-, then alpha and F*) read r_up at their own row and,
+// shifted by the column offset, at the rows of their lower neighbours.  On
+// GB300 the FP64 pipe, not HBM, bounds these passes, so each pair costs as few
+// FP64 operations as the formulas allow and every comparison, min and max runs
+// on the integer pipe (kernels_common.cuh).
 #include "afc_internal.h"
 #include "kernels_common.cuh"
 
@@ -15,15 +21,17 @@ namespace {
 
 // y = AA u;  udot^L = (f - y) / m (0 at Dirichlet nodes, whose data is constant);
 // predictor u~ = u + dt (f - y) / m, u~ = u_D at Dirichlet nodes.
+template <int KT>
 __global__ void k_ssp_rate(int64_t N, Offsets of, const double* __restrict__ AA, const double* __restrict__ u,
                            const double* __restrict__ f, const double* __restrict__ mL,
                            const uint8_t* __restrict__ dir, const double* __restrict__ udir, double dt,
                            double* __restrict__ udot, double* __restrict__ ut) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   double y = 0.0;
-#pragma unroll 4
-  for (int k = 0; k < of.K; ++k) y = fma(AA[k * N + i], u[i + of.o[k]], y);
+#pragma unroll
+  for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], u[i + of.o[k]], y);
   if (dir[i]) {
     udot[i] = 0.0;
     ut[i] = udir[i];
@@ -34,47 +42,64 @@ __global__ void k_ssp_rate(int64_t N, Offsets of, const double* __restrict__ AA,
   }
 }
 
-// Zalesak steps 1-3: P+/-, Q+/- (neighbours of the predictor), R+/-.
+// Eq. defn_r_ij_SSP for every pair i < j: r_ij = m_ij (udot_i - udot_j) + d_ij (u_j - u_i).
+// Pairs outside the pattern have m = d = 0 and get r = 0.
+template <int KT>
+__global__ void k_ssp_edges(int64_t N, Offsets of, const double* __restrict__ m_up, const double* __restrict__ d_up,
+                            const double* __restrict__ u, const double* __restrict__ udot,
+                            double* __restrict__ r_up) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double ui = u[i], udi = udot[i];
+#pragma unroll
+  for (int ku = 0; ku < Kup; ++ku) {
+    const int64_t q = (int64_t)ku * N + i;
+    const int64_t j = i + of.o[Kup + 1 + ku];
+    r_up[q] = fma(m_up[q], udi - udot[j], d_up[q] * (u[j] - ui));
+  }
+}
+
+// Zalesak steps 1-3: P+/- from the stored fluxes, Q+/- from the predictor over N_i, R+/-.
+template <int KT>
 __global__ void k_ssp_factors(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
-                              const double* __restrict__ m_up, const double* __restrict__ d_up,
-                              const double* __restrict__ u, const double* __restrict__ udot,
-                              const double* __restrict__ ut, const double* __restrict__ mL,
-                              const uint8_t* __restrict__ dir, double dt, double* __restrict__ Rp,
-                              double* __restrict__ Rm) {
+                              const double* __restrict__ r_up, const double* __restrict__ ut,
+                              const double* __restrict__ mL, const uint8_t* __restrict__ dir, double dt,
+                              double* __restrict__ Rp, double* __restrict__ Rm) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
   const unsigned long long mk = mask[i];
-  const double ui = u[i], udi = udot[i], uti = ut[i];
+  const double uti = ut[i];
   double Pp = 0.0, Pm = 0.0, tmax = uti, tmin = uti;
-  for (int k = 0; k < of.K; ++k) {
-    if (k == of.Kup || !((mk >> k) & 1ull)) continue;
-    const int64_t j = i + of.o[k];
-    double m, d;
-    pair_coef(of, k, i, N, m_up, d_up, m, d);
-    const double r = m * (udi - udot[j]) + d * (u[j] - ui);
-    if (r > 0.0) Pp += r; else Pm += r;
-    const double utj = ut[j];
-    tmax = fmax(tmax, utj);
-    tmin = fmin(tmin, utj);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (k == Kup || !((mk >> k) & 1ull)) continue;
+    const double r = pair_flux(of, Kup, k, i, N, r_up);
+    if (gt0(r)) Pp += r;
+    else if (!is0(r)) Pm += r;
+    const double utj = ut[i + of.o[k]];
+    tmax = imax(tmax, utj);
+    tmin = imin(tmin, utj);
   }
   const double Qp = tmax - uti, Qm = tmin - uti;     // >= 0 and <= 0: the max/min include i itself
   const double m = mL[i];
-  Rp[i] = Pp != 0.0 ? fmin(1.0, m * Qp / (dt * Pp)) : 1.0;
-  Rm[i] = Pm != 0.0 ? fmin(1.0, m * Qm / (dt * Pm)) : 1.0;
+  Rp[i] = zalesak_factor(m * Qp, dt * Pp);
+  Rm[i] = zalesak_factor(m * Qm, dt * Pm);
 }
 
 // Zalesak step 4 and the update: F*_i = sum_j alpha_ij r_ij,
 // u_new = u~ + dt F* / m (= u + dt (f + F* - AA u) / m, Eq. FE-SSP), Dirichlet: u_D;
 // out = a * uA + b * u_new (the SSP combination of the stage).
+template <int KT>
 __global__ void k_ssp_correct(int64_t N, Offsets of, int limiter, const unsigned long long* __restrict__ mask,
-                              const double* __restrict__ m_up, const double* __restrict__ d_up,
-                              const double* __restrict__ u, const double* __restrict__ udot,
-                              const double* __restrict__ ut, const double* __restrict__ Rp,
-                              const double* __restrict__ Rm, const double* __restrict__ mL,
-                              const uint8_t* __restrict__ dir, const double* __restrict__ udir, double dt, double a,
-                              const double* __restrict__ uA, double b, double* __restrict__ out,
-                              double* __restrict__ Fout) {
+                              const double* __restrict__ r_up, const double* __restrict__ ut,
+                              const double* __restrict__ Rp, const double* __restrict__ Rm,
+                              const double* __restrict__ mL, const uint8_t* __restrict__ dir,
+                              const double* __restrict__ udir, double dt, double a, const double* __restrict__ uA,
+                              double b, double* __restrict__ out, double* __restrict__ Fout) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   double unew;
@@ -82,18 +107,20 @@ __global__ void k_ssp_correct(int64_t N, Offsets of, int limiter, const unsigned
   if (dir[i]) {
     unew = udir[i];
   } else {
-    const unsigned long long mk = mask[i];
-    const double ui = u[i], udi = udot[i], rpi = Rp[i], rmi = Rm[i];
     if (limiter != AFC_LIM_NONE) {
-      for (int k = 0; k < of.K; ++k) {
-        if (k == of.Kup || !((mk >> k) & 1ull)) continue;
-        const int64_t j = i + of.o[k];
-        double m, d;
-        pair_coef(of, k, i, N, m_up, d_up, m, d);
-        const double r = m * (udi - udot[j]) + d * (u[j] - ui);
-        double alpha = 1.0;
-        if (limiter == AFC_LIM_ZALESAK) alpha = r > 0.0 ? fmin(rpi, Rm[j]) : fmin(rmi, Rp[j]);
-        F = fma(alpha, r, F);
+      const unsigned long long mk = mask[i];
+      const double rpi = Rp[i], rmi = Rm[i];
+    #pragma unroll
+  for (int k = 0; k < K; ++k) {
+        if (k == Kup || !((mk >> k) & 1ull)) continue;
+        const double r = pair_flux(of, Kup, k, i, N, r_up);
+        if (limiter == AFC_LIM_ZALESAK) {
+          const int64_t j = i + of.o[k];
+          const double alpha = gt0(r) ? imin_nn(rpi, Rm[j]) : imin_nn(rmi, Rp[j]);
+          F = fma(alpha, r, F);
+        } else {
+          F += r;
+        }
       }
     }
     unew = ut[i] + dt * F / mL[i];
@@ -106,106 +133,142 @@ __global__ void k_ssp_correct(int64_t N, Offsets of, int limiter, const unsigned
 
 // Once per step: y = AA u_old, predictor u~ = u_old - (dt/2)(y - f)/m (Eq. forward_euler,
 // u_D at Dirichlet nodes), b0 = (m/dt) u_old - y/2 + f (right-hand side of Eq. CNZal).
+template <int KT>
 __global__ void k_cn_predictor(int64_t N, Offsets of, const double* __restrict__ AA, const double* __restrict__ uo,
                                const double* __restrict__ f, const double* __restrict__ mL,
                                const uint8_t* __restrict__ dir, const double* __restrict__ udir, double dt,
                                double* __restrict__ ut, double* __restrict__ b0) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   double y = 0.0;
-#pragma unroll 4
-  for (int k = 0; k < of.K; ++k) y = fma(AA[k * N + i], uo[i + of.o[k]], y);
+#pragma unroll
+  for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], uo[i + of.o[k]], y);
   const double m = mL[i];
   ut[i] = dir[i] ? udir[i] : uo[i] - 0.5 * dt * (y - f[i]) / m;
   b0[i] = (m / dt * uo[i] - 0.5 * y) + f[i];
 }
 
-// Q+/- of the CN predictor (fixed for the whole step).
+// Q+/- of the CN predictor over N_i (fixed for the whole step).
+template <int KT>
 __global__ void k_bounds_of(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
                             const double* __restrict__ v, double* __restrict__ Qp, double* __restrict__ Qm) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const unsigned long long mk = mask[i];
   const double vi = v[i];
   double tmax = vi, tmin = vi;
-  for (int k = 0; k < of.K; ++k) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
     if (!((mk >> k) & 1ull)) continue;
     const double vj = v[i + of.o[k]];
-    tmax = fmax(tmax, vj);
-    tmin = fmin(tmin, vj);
+    tmax = imax(tmax, vj);
+    tmin = imin(tmin, vj);
   }
   Qp[i] = tmax - vi;
   Qm[i] = tmin - vi;
 }
 
-// CN flux Eq. flux_002 for the pair (i, j), prelimited by Eq. prelimiting (L = 2)
-// against twice its diffusive part evaluated at the CN average.
-__device__ __forceinline__ double cn_flux(double m, double d, double dt, double uni, double uoi, double unj,
-                                          double uoj, int prelimit) {
-  double r = (m / dt) * ((uni - uoi) - (unj - uoj)) + (0.5 * d) * ((unj + uoj) - (uni + uoi));
-  if (prelimit) {
-    const double lim = (2.0 * d) * (0.5 * (unj + uoj) - 0.5 * (uni + uoi));
-    r = minmod(r, lim);
+// Node sums of the CN flux: a = u - u_old, s = u + u_old; optionally first
+// u += omega * delta (the damped update of Sec. 4).
+__global__ void k_cn_update(int64_t N, double omega, const double* __restrict__ delta, double* __restrict__ u,
+                            const double* __restrict__ uo, double* __restrict__ a, double* __restrict__ s) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double ui = u[i];
+  if (delta) {
+    ui = ui + omega * delta[i];
+    u[i] = ui;
   }
-  return r;
+  const double uoi = uo[i];
+  a[i] = ui - uoi;
+  s[i] = ui + uoi;
+}
+
+// Eq. flux_002 for every pair i < j, prelimited by Eq. prelimiting (L = 2) against twice
+// its diffusive part at the CN average:  q = d_ij (s_j - s_i) = 2 d_ij (ubar_j - ubar_i),
+// r = (m_ij / dt)(a_i - a_j) + q / 2,  r <- minmod(r, q).
+template <int KT>
+__global__ void k_cn_edges(int64_t N, Offsets of, const double* __restrict__ mdt_up, const double* __restrict__ d_up,
+                           const double* __restrict__ a, const double* __restrict__ s, int prelimit,
+                           double* __restrict__ r_up) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double ai = a[i], si = s[i];
+#pragma unroll
+  for (int ku = 0; ku < Kup; ++ku) {
+    const int64_t q = (int64_t)ku * N + i;
+    const int64_t j = i + of.o[Kup + 1 + ku];
+    const double lim = d_up[q] * (s[j] - si);
+    double r = fma(mdt_up[q], ai - a[j], half_exact(lim));
+    if (prelimit) r = minmod(r, lim);
+    r_up[q] = r;
+  }
 }
 
 // Zalesak steps 1-3 for the CN fluxes (Q+/- precomputed from the predictor).
+template <int KT>
 __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
-                             const double* __restrict__ m_up, const double* __restrict__ d_up,
-                             const double* __restrict__ un, const double* __restrict__ uo,
-                             const double* __restrict__ Qp, const double* __restrict__ Qm,
-                             const double* __restrict__ mL, const uint8_t* __restrict__ dir, double dt, int prelimit,
-                             double* __restrict__ Rp, double* __restrict__ Rm) {
+                             const double* __restrict__ r_up, const double* __restrict__ Qp,
+                             const double* __restrict__ Qm, const double* __restrict__ mL,
+                             const uint8_t* __restrict__ dir, double dt, double* __restrict__ Rp,
+                             double* __restrict__ Rm) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
   const unsigned long long mk = mask[i];
-  const double uni = un[i], uoi = uo[i];
   double Pp = 0.0, Pm = 0.0;
-  for (int k = 0; k < of.K; ++k) {
-    if (k == of.Kup || !((mk >> k) & 1ull)) continue;
-    const int64_t j = i + of.o[k];
-    double m, d;
-    pair_coef(of, k, i, N, m_up, d_up, m, d);
-    const double r = cn_flux(m, d, dt, uni, uoi, un[j], uo[j], prelimit);
-    if (r > 0.0) Pp += r; else Pm += r;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (k == Kup || !((mk >> k) & 1ull)) continue;
+    const double r = pair_flux(of, Kup, k, i, N, r_up);
+    if (gt0(r)) Pp += r;
+    else if (!is0(r)) Pm += r;
   }
   const double m = mL[i];
-  Rp[i] = Pp != 0.0 ? fmin(1.0, m * Qp[i] / (dt * Pp)) : 1.0;
-  Rm[i] = Pm != 0.0 ? fmin(1.0, m * Qm[i] / (dt * Pm)) : 1.0;
+  Rp[i] = zalesak_factor(m * Qp[i], dt * Pp);
+  Rm[i] = zalesak_factor(m * Qm[i], dt * Pm);
 }
 
 // Zalesak step 4, F*, and the nonlinear residual of Eq. CNZal:
 // res = b0 + F* - (m/dt u + AA u / 2) on free rows, 0 on Dirichlet rows;
 // block partial sums of res^2 for the stopping test.
+template <int KT>
 __global__ void k_cn_residual(int64_t N, Offsets of, int limiter, const unsigned long long* __restrict__ mask,
-                              const double* __restrict__ m_up, const double* __restrict__ d_up,
-                              const double* __restrict__ AA, const double* __restrict__ un,
-                              const double* __restrict__ uo, const double* __restrict__ Rp,
+                              const double* __restrict__ r_up, const double* __restrict__ AA,
+                              const double* __restrict__ un, const double* __restrict__ Rp,
                               const double* __restrict__ Rm, const double* __restrict__ b0,
-                              const double* __restrict__ mL, const uint8_t* __restrict__ dir, double dt, int prelimit,
+                              const double* __restrict__ mLdt, const uint8_t* __restrict__ dir,
                               double* __restrict__ res, double* __restrict__ Fout, double* __restrict__ part) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double r2 = 0.0;
   if (i < N) {
     double rv = 0.0, F = 0.0;
     if (!dir[i]) {
       const unsigned long long mk = mask[i];
-      const double uni = un[i], uoi = uo[i];
       double y = 0.0;
-      for (int k = 0; k < of.K; ++k) {
-        const int64_t j = i + of.o[k];
-        y = fma(AA[k * N + i], un[j], y);
-        if (limiter == AFC_LIM_NONE || k == of.Kup || !((mk >> k) & 1ull)) continue;
-        double m, d;
-        pair_coef(of, k, i, N, m_up, d_up, m, d);
-        const double r = cn_flux(m, d, dt, uni, uoi, un[j], uo[j], prelimit);
-        double alpha = 1.0;
-        if (limiter == AFC_LIM_ZALESAK) alpha = r > 0.0 ? fmin(Rp[i], Rm[j]) : fmin(Rm[i], Rp[j]);
-        F = fma(alpha, r, F);
+    #pragma unroll
+  for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], un[i + of.o[k]], y);
+      if (limiter != AFC_LIM_NONE) {
+        const double rpi = Rp[i], rmi = Rm[i];
+      #pragma unroll
+  for (int k = 0; k < K; ++k) {
+          if (k == Kup || !((mk >> k) & 1ull)) continue;
+          const double r = pair_flux(of, Kup, k, i, N, r_up);
+          if (limiter == AFC_LIM_ZALESAK) {
+            const int64_t j = i + of.o[k];
+            const double alpha = gt0(r) ? imin_nn(rpi, Rm[j]) : imin_nn(rmi, Rp[j]);
+            F = fma(alpha, r, F);
+          } else {
+            F += r;
+          }
+        }
       }
-      rv = b0[i] + F - (mL[i] / dt * uni + 0.5 * y);
+      rv = b0[i] + F - (mLdt[i] * un[i] + 0.5 * y);
     }
     res[i] = rv;
     if (Fout) Fout[i] = F;
@@ -221,13 +284,21 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
-  AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, uin, p->f.p, p->mL.p, p->dir.p, p->udir.p, dt, p->udot.p,
-                                  p->ut.p));
-  if (limiter == AFC_LIM_ZALESAK)
-    AFC_LAUNCH(p, "k_ssp_factors", k_ssp_factors<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->m_up.p, p->d_up.p, uin, p->udot.p, p->ut.p, p->mL.p,
-                                       p->dir.p, dt, p->Rp.p, p->Rm.p));
-  AFC_LAUNCH(p, "k_ssp_correct", k_ssp_correct<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->m_up.p, p->d_up.p, uin, p->udot.p, p->ut.p,
-                                     p->Rp.p, p->Rm.p, p->mL.p, p->dir.p, p->udir.p, dt, a, uA, b, out, p->Fs.p));
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, uin, p->f.p, p->mL.p,
+                                                                     p->dir.p, p->udir.p, dt, p->udot.p, p->ut.p));
+    if (limiter != AFC_LIM_NONE)
+      AFC_LAUNCH(p, "k_ssp_edges", k_ssp_edges<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->m_up.p, p->d_up.p, uin,
+                                                                         p->udot.p, p->r_up.p));
+    if (limiter == AFC_LIM_ZALESAK)
+      AFC_LAUNCH(p, "k_ssp_factors", k_ssp_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->ut.p,
+                                                                             p->mL.p, p->dir.p, dt, p->Rp.p, p->Rm.p));
+    AFC_LAUNCH(p, "k_ssp_correct",
+               k_ssp_correct<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->r_up.p, p->ut.p, p->Rp.p,
+                                                      p->Rm.p, p->mL.p, p->dir.p, p->udir.p, dt, a, uA, b, out,
+                                                      p->Fs.p));
+  });
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
@@ -236,24 +307,44 @@ int cn_predictor(afc_problem_s* p, const double* u_old, double dt) {
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
-  AFC_LAUNCH(p, "k_cn_predictor", k_cn_predictor<<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, u_old, p->f.p, p->mL.p, p->dir.p, p->udir.p, dt, p->ut.p,
-                                      p->b0.p));
-  AFC_LAUNCH(p, "k_bounds_of", k_bounds_of<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->ut.p, p->Qp.p, p->Qm.p));
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    AFC_LAUNCH(p, "k_cn_predictor", k_cn_predictor<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, u_old, p->f.p,
+                                                                             p->mL.p, p->dir.p, p->udir.p, dt, p->ut.p,
+                                                                             p->b0.p));
+    AFC_LAUNCH(p, "k_bounds_of",
+               k_bounds_of<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->ut.p, p->Qp.p, p->Qm.p));
+  });
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
 
-int cn_limited_residual(afc_problem_s* p, const double* u_new, const double* u_old, double dt, int limiter,
-                        int prelimit, double* res, double* normsq_slot) {
+int cn_update(afc_problem_s* p, double omega, const double* delta, double* u, const double* u_old) {
+  AFC_LAUNCH(p, "k_cn_update", k_cn_update<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, omega, delta, u, u_old,
+                                                                                       p->cn_a.p, p->cn_s.p));
+  AFC_CUDA(cudaGetLastError());
+  return AFC_OK;
+}
+
+int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int limiter, int prelimit, double* res,
+                        double* normsq_slot) {
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
-  if (limiter == AFC_LIM_ZALESAK)
-    AFC_LAUNCH(p, "k_cn_factors", k_cn_factors<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->m_up.p, p->d_up.p, u_new, u_old, p->Qp.p, p->Qm.p,
-                                      p->mL.p, p->dir.p, dt, prelimit, p->Rp.p, p->Rm.p));
-  AFC_LAUNCH(p, "k_cn_residual", k_cn_residual<<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->m_up.p, p->d_up.p, p->AA.p, u_new, u_old,
-                                     p->Rp.p, p->Rm.p, p->b0.p, p->mL.p, p->dir.p, dt, prelimit, res, p->Fs.p,
-                                     p->part.p));
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    if (limiter != AFC_LIM_NONE)
+      AFC_LAUNCH(p, "k_cn_edges", k_cn_edges<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mdt_up.p, p->d_up.p, p->cn_a.p,
+                                                                       p->cn_s.p, prelimit, p->r_up.p));
+    if (limiter == AFC_LIM_ZALESAK)
+      AFC_LAUNCH(p, "k_cn_factors", k_cn_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->Qp.p,
+                                                                           p->Qm.p, p->mL.p, p->dir.p, dt, p->Rp.p,
+                                                                           p->Rm.p));
+    AFC_LAUNCH(p, "k_cn_residual",
+               k_cn_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->r_up.p, p->AA.p, u_new,
+                                                      p->Rp.p, p->Rm.p, p->b0.p, p->mLdt.p, p->dir.p, res, p->Fs.p,
+                                                      p->part.p));
+  });
   finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;

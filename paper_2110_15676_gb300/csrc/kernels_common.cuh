@@ -1,6 +1,8 @@
 // Small device helpers shared by the hot-path kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "afc_internal.h"
 
 namespace afc {
@@ -23,11 +25,62 @@ __device__ __forceinline__ double pair_d(const Offsets& of, int k, int64_t i, in
   return d_up[(int64_t)(of.Kup - 1 - k) * N + i + of.o[k]];
 }
 
+// ---- comparisons on the integer pipe ----------------------------------------
+// GB300 runs FP64 compares, min/max and arithmetic on a pipe that issues 2 thread
+// operations per SM and cycle.  Comparisons of finite doubles are done here on
+// their bit patterns instead: key() maps a double to an int64 with the same
+// order (-0 sorts just below +0), so every decision below is exact.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }      // x > 0
+__device__ __forceinline__ bool lt0(double x) { return dkey(x) < -1; }                      // x < 0
+__device__ __forceinline__ bool is0(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ double imin(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }
+__device__ __forceinline__ double imax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+// min / max of two values known to be >= 0 (correction factors, bounds): plain int compare
+__device__ __forceinline__ double imin_nn(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
+}
+// exact 0.5 * x and 2 * x by moving the exponent (normal numbers); FP64 fallback otherwise
+__device__ __forceinline__ double half_exact(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long e = (b >> 52) & 0x7ff;
+  if (e > 1 && e < 0x7ff) return __longlong_as_double(b - (1LL << 52));
+  return 0.5 * x;
+}
+__device__ __forceinline__ double twice_exact(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long e = (b >> 52) & 0x7ff;
+  if (e > 0 && e < 0x7fe) return __longlong_as_double(b + (1LL << 52));
+  return x + x;
+}
+
+// R = min{1, num / den} of Zalesak's step 3 for num = m_i Q, den = dt P of the same sign,
+// R = 1 if P = 0.  For same-sign num, den the rounded quotient reaches 1 exactly when
+// |num| >= |den|, so the division is only done where R < 1 (same result bit for bit).
+__device__ __forceinline__ double zalesak_factor(double num, double den) {
+  if (is0(den)) return 1.0;
+  const long long an = __double_as_longlong(num) & 0x7fffffffffffffffLL;
+  const long long ad = __double_as_longlong(den) & 0x7fffffffffffffffLL;
+  if (an >= ad) return 1.0;
+  return num / den;
+}
+
 // minmod of Eq. prelimiting: 0 unless both arguments have the same strict sign.
 __device__ __forceinline__ double minmod(double a, double b) {
-  if (a > 0.0 && b > 0.0) return fmin(a, b);
-  if (a < 0.0 && b < 0.0) return fmax(a, b);
+  if (gt0(a) && gt0(b)) return imin(a, b);
+  if (lt0(a) && lt0(b)) return imax(a, b);
   return 0.0;
+}
+
+// The antidiffusive flux of the pair (i, i + o_k) seen from row i, for a flux
+// stored once per pair at the pair's lower row: r_ij = r_e (k > Kup) or -r_e.
+__device__ __forceinline__ double pair_flux(const Offsets& of, int Kup, int k, int64_t i, int64_t N,
+                                            const double* __restrict__ r_up) {
+  if (k > Kup) return r_up[(int64_t)(k - Kup - 1) * N + i];
+  return -r_up[(int64_t)(Kup - 1 - k) * N + i + of.o[k]];
 }
 
 template <class T>
@@ -75,6 +128,16 @@ __device__ __forceinline__ void block_sums_to(double (&v)[NV], double* part, int
     }
   }
   __syncthreads();
+}
+
+// Run f(std::integral_constant<int, K>) with K fixed at compile time for the two
+// structured patterns (15 offsets: Kuhn P1, 27: Q1) so that the per-row loops
+// unroll completely and all loads of a row are in flight together; 0 = any K.
+template <class F>
+inline void with_K(int K, F&& f) {
+  if (K == 15) f(std::integral_constant<int, 15>{});
+  else if (K == 27) f(std::integral_constant<int, 27>{});
+  else f(std::integral_constant<int, 0>{});
 }
 
 // out[0] = sum of part[0..n) in a fixed order (one block).

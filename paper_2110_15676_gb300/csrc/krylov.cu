@@ -107,14 +107,26 @@ __global__ void k_minmax(int64_t N, const double* __restrict__ x, double* __rest
 }
 
 __global__ void k_minmax_fin(const double* __restrict__ part, int n, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+  __shared__ double smn[kBlock], smx[kBlock];
   double mn = INFINITY, mx = -INFINITY;
-  for (int q = 0; q < n; ++q) {
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
     mn = fmin(mn, part[2 * q]);
     mx = fmax(mx, part[2 * q + 1]);
   }
-  out[0] = mn;
-  out[1] = mx;
+  smn[threadIdx.x] = mn;
+  smx[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + s]);
+      smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = smn[0];
+    out[1] = smx[0];
+  }
 }
 
 template <class T, class TV>
@@ -144,7 +156,7 @@ int axpy_device(afc_problem_s* p, double a, const double* x, double* y) {
 
 int minmax_device(afc_problem_s* p, const double* x, double* mn, double* mx) {
   AFC_LAUNCH(p, "k_minmax", k_minmax<<<kRedBlocks, kBlock, 0, p->stream>>>(p->N, x, p->part.p));
-  AFC_LAUNCH(p, "k_minmax_fin", k_minmax_fin<<<1, 32, 0, p->stream>>>(p->part.p, kRedBlocks, p->scal.p + 60));
+  AFC_LAUNCH(p, "k_minmax_fin", k_minmax_fin<<<1, kBlock, 0, p->stream>>>(p->part.p, kRedBlocks, p->scal.p + 60));
   AFC_CUDA(cudaGetLastError());
   AFC_CUDA(cudaMemcpyAsync(p->host_scal + 60, p->scal.p + 60, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   AFC_CUDA(cudaStreamSynchronize(p->stream));
@@ -167,8 +179,8 @@ constexpr int kMaxRestart = 64;
 // device scalar slots
 enum : int {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_TOL, S_NRES, S_N0, S_ITS, S_DONE, S_MAXIT,
-  S_BETA, S_K_USED, S_INVH, S_CYCLE_DONE, S_FIRST,
-  S_CS = 16, S_SN = S_CS + kMaxRestart, S_G = S_SN + kMaxRestart, S_Y = S_G + kMaxRestart + 1,
+  S_BETA, S_K_USED, S_INVH, S_CYCLE_DONE, S_FIRST, S_ATOL, S_RTOL,
+  S_CS = 20, S_SN = S_CS + kMaxRestart, S_G = S_SN + kMaxRestart, S_Y = S_G + kMaxRestart + 1,
   S_H1 = S_Y + kMaxRestart, S_H2 = S_H1 + kMaxRestart + 1, S_HCOL = S_H2 + kMaxRestart + 1,
   S_END = S_HCOL + (kMaxRestart + 1) * kMaxRestart
 };
@@ -179,20 +191,73 @@ struct KrylovWork {
   int pad = 0, m = 0, fp32 = -1;
   DBuf<char> vec;       // all vectors (with halos)
   DBuf<double> sc, part;
+  DBuf<unsigned int> counter;
   double* hsc = nullptr;
   size_t vstride = 0;   // elements per vector incl. halo
-  void* vptr(int q) { return vec.base + q * vstride * (fp32 ? sizeof(float) : sizeof(double)); }
 };
 
 template struct DBuf<char>;
+template struct DBuf<unsigned int>;
 
 namespace {
 
-// ---- BiCGStab ----
+// ---- "last block" reductions ------------------------------------------------
+// A producer kernel writes one partial per block and counts finished blocks; the
+// block that finishes last sums all partials in block order (deterministic) and
+// updates the solver scalars.  Every block reads the scalars it needs before it
+// counts itself, and only the last block writes them, so no block of a kernel
+// sees a scalar that the same kernel changes.
+// Sum v over the block in a fixed order; every thread receives the total.
+__device__ __forceinline__ double block_allsum(double v) {
+  __shared__ double sh[32];
+  __shared__ double total;
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) total = t;
+  }
+  __syncthreads();
+  const double r = total;
+  __syncthreads();
+  return r;
+}
+
+template <int NV>
+__device__ __forceinline__ bool last_block_sums(double (&v)[NV], double* part, int64_t pstride,
+                                                unsigned int* counter, double (&tot)[NV]) {
+  block_sums_to<NV>(v, part, pstride);
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int done = atomicAdd(counter, 1u);
+    am_last = done == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  const int n = gridDim.x;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) s += __ldcg(part + q * pstride + b);
+    tot[q] = block_allsum(s);
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+__device__ __forceinline__ bool stop_test(double nr, const double* sc) { return nr < sc[S_TOL]; }
+
+// ---- BiCGStab (van der Vorst 1992), Jacobi preconditioner on the directions ----
 template <class T>
 __global__ void k_bicg_init(int64_t N, const double* __restrict__ rhs, T* x, T* r, T* rh, T* p, T* v,
-                            double* __restrict__ part) {
-  double acc = 0.0;
+                            double* __restrict__ part, unsigned int* counter, double* sc) {
+  double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = (T)rhs[i];
     x[i] = 0;
@@ -200,33 +265,25 @@ __global__ void k_bicg_init(int64_t N, const double* __restrict__ rhs, T* x, T* 
     rh[i] = ri;
     p[i] = 0;
     v[i] = 0;
-    acc += (double)ri * (double)ri;
+    acc[0] += (double)ri * (double)ri;
   }
-  block_sum_to(acc, part);
-}
-
-__global__ void k_bicg_init_fin(const double* __restrict__ part, int n, double* sc, double atol, double rtol,
-                                int maxit) {
-  __shared__ double tot;
-  double v = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) v += part[q];
-  block_sum_to(v, sc + S_END);   // scratch slot past the named ones
+  double tot[1];
+  if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
-    tot = sc[S_END];
-    const double n0 = sqrt(tot);
+    const double n0 = sqrt(tot[0]);
     sc[S_N0] = n0;
     sc[S_NRES] = n0;
-    sc[S_RHO] = tot;
+    sc[S_RHO] = tot[0];
     sc[S_RHO_OLD] = 1.0;
     sc[S_ALPHA] = 1.0;
     sc[S_OMEGA] = 1.0;
-    sc[S_TOL] = fmax(atol, rtol * n0);
+    sc[S_TOL] = fmax(sc[S_ATOL], sc[S_RTOL] * n0);
     sc[S_ITS] = 0.0;
-    sc[S_MAXIT] = (double)maxit;
-    sc[S_DONE] = !isfinite(n0) ? 2.0 : (n0 < sc[S_TOL] ? 1.0 : (maxit <= 0 ? 4.0 : 0.0));
+    sc[S_DONE] = !isfinite(n0) ? 2.0 : (n0 < sc[S_TOL] ? 1.0 : (sc[S_MAXIT] <= 0.0 ? 4.0 : 0.0));
   }
 }
 
+// p = r + beta (p - omega v), phat = D^{-1} p
 template <class T>
 __global__ void k_bicg_p(int64_t N, const double* __restrict__ sc, const T* __restrict__ r, T* p,
                          const T* __restrict__ v, const T* __restrict__ dinv, T* __restrict__ ph) {
@@ -240,109 +297,96 @@ __global__ void k_bicg_p(int64_t N, const double* __restrict__ sc, const T* __re
   }
 }
 
-// y = B x (row i), plus block partials of sum(a * y) (one dot) or of (y.s, y.y) (two dots)
-template <class T, int NDOT>
-__global__ void k_bicg_spmv(int64_t N, Offsets of, const double* __restrict__ sc, const T* __restrict__ B,
-                            const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ a,
-                            double* __restrict__ part, int64_t pstride) {
+// v = B phat and (rhat, v); the last block sets alpha = rho / (rhat, v)
+template <int KT, class T>
+__global__ void k_bicg_spmv1(int64_t N, Offsets of, double* sc, const T* __restrict__ B, const T* __restrict__ x,
+                             T* __restrict__ y, const T* __restrict__ a, double* __restrict__ part,
+                             unsigned int* counter) {
   if (sc[S_DONE] != 0.0) return;
+  const int K = KT > 0 ? KT : of.K;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double acc[NDOT];
-#pragma unroll
-  for (int q = 0; q < NDOT; ++q) acc[q] = 0.0;
+  double acc[1] = {0.0};
   if (i < N) {
     T s = 0;
-#pragma unroll 4
-    for (int k = 0; k < of.K; ++k) s = fma(B[k * N + i], x[i + of.o[k]], s);
+#pragma unroll
+    for (int k = 0; k < K; ++k) s = fma(B[k * N + i], x[i + of.o[k]], s);
     y[i] = s;
-    if (NDOT == 1) {
-      acc[0] = (double)a[i] * (double)s;
-    } else {
-      acc[0] = (double)s * (double)a[i];
-      acc[NDOT - 1] = (double)s * (double)s;
-    }
+    acc[0] = (double)a[i] * (double)s;
   }
-  block_sums_to<NDOT>(acc, part, pstride);
-}
-
-__global__ void k_bicg_fin_alpha(const double* __restrict__ part, int n, double* sc) {
-  if (sc[S_DONE] != 0.0) return;
-  double v = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) v += part[q];
-  block_sum_to(v, sc + S_END);
+  double tot[1];
+  if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
-    const double rv = sc[S_END];
-    const double al = sc[S_RHO] / rv;
-    if (!isfinite(al) || rv == 0.0) sc[S_DONE] = 2.0;
+    const double al = sc[S_RHO] / tot[0];
+    if (!isfinite(al) || tot[0] == 0.0) sc[S_DONE] = 2.0;
     else sc[S_ALPHA] = al;
   }
 }
 
+// s = r - alpha v, shat = D^{-1} s, ||s||; the last block tests convergence at s
 template <class T>
-__global__ void k_bicg_s(int64_t N, const double* __restrict__ sc, const T* __restrict__ r, const T* __restrict__ v,
-                         const T* __restrict__ dinv, T* __restrict__ s, T* __restrict__ sh, double* __restrict__ part) {
+__global__ void k_bicg_s(int64_t N, double* sc, const T* __restrict__ r, const T* __restrict__ v,
+                         const T* __restrict__ dinv, T* __restrict__ s, T* __restrict__ sh, double* __restrict__ part,
+                         unsigned int* counter) {
   if (sc[S_DONE] != 0.0) return;
   const T al = (T)sc[S_ALPHA];
-  double acc = 0.0;
+  double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const T si = r[i] - al * v[i];
     s[i] = si;
     sh[i] = dinv[i] * si;
-    acc += (double)si * (double)si;
+    acc[0] += (double)si * (double)si;
   }
-  block_sum_to(acc, part);
-}
-
-__global__ void k_bicg_fin_s(const double* __restrict__ part, int n, double* sc) {
-  if (sc[S_DONE] != 0.0) return;
-  double v = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) v += part[q];
-  block_sum_to(v, sc + S_END);
+  double tot[1];
+  if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
-    const double ns = sqrt(sc[S_END]);
+    const double ns = sqrt(tot[0]);
     if (!isfinite(ns)) { sc[S_DONE] = 2.0; return; }
-    if (ns < sc[S_TOL]) {
+    if (stop_test(ns, sc)) {
       sc[S_NRES] = ns;
       sc[S_ITS] += 1.0;
-      sc[S_DONE] = 3.0;     // converged at s: x += alpha phat still to do
+      sc[S_DONE] = 3.0;     // converged at s: x += alpha phat in the next kernel
     }
   }
 }
 
-// x += alpha phat once, when the solve converged at s
-template <class T>
-__global__ void k_bicg_early_x(int64_t N, const double* __restrict__ sc, T* __restrict__ x, const T* __restrict__ ph) {
-  if (sc[S_DONE] != 3.0) return;
-  const T al = (T)sc[S_ALPHA];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = x[i] + al * ph[i];
-}
-
-__global__ void k_bicg_fin_omega(const double* __restrict__ part, int n, int64_t pstride, double* sc) {
-  if (sc[S_DONE] == 3.0) {
-    if (threadIdx.x == 0) sc[S_DONE] = 1.0;
-    return;
+// t = B shat, (t, s), (t, t); the last block sets omega.  When the solve converged at
+// s, this kernel instead finishes x += alpha phat.
+template <int KT, class T>
+__global__ void k_bicg_spmv2(int64_t N, Offsets of, double* sc, const T* __restrict__ B, const T* __restrict__ sh,
+                             T* __restrict__ t, const T* __restrict__ s, T* __restrict__ x,
+                             const T* __restrict__ ph, double* __restrict__ part, unsigned int* counter) {
+  const double done = sc[S_DONE];
+  if (done != 0.0 && done != 3.0) return;
+  const int K = KT > 0 ? KT : of.K;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc[2] = {0.0, 0.0};
+  if (done == 3.0) {
+    if (i < N) x[i] = x[i] + (T)sc[S_ALPHA] * ph[i];
+  } else if (i < N) {
+    T v = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v = fma(B[k * N + i], sh[i + of.o[k]], v);
+    t[i] = v;
+    acc[0] = (double)v * (double)s[i];
+    acc[1] = (double)v * (double)v;
   }
-  if (sc[S_DONE] != 0.0) return;
-  double v0 = 0.0, v1 = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    v0 += part[q];
-    v1 += part[pstride + q];
-  }
-  double vv[2] = {v0, v1};
-  block_sums_to<2>(vv, sc + S_END, 1);
+  double tot[2];
+  if (!last_block_sums<2>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
-    const double ts = sc[S_END], tt = sc[S_END + 1];
-    const double om = ts / tt;
-    if (!isfinite(om) || tt == 0.0) sc[S_DONE] = 2.0;
+    if (done == 3.0) { sc[S_DONE] = 1.0; return; }
+    const double om = tot[0] / tot[1];
+    if (!isfinite(om) || tot[1] == 0.0) sc[S_DONE] = 2.0;
     else sc[S_OMEGA] = om;
   }
 }
 
+// x += alpha phat + omega shat, r = s - omega t, ||r||, (rhat, r); the last block tests
+// convergence and rotates rho
 template <class T>
-__global__ void k_bicg_xr(int64_t N, const double* __restrict__ sc, T* __restrict__ x, const T* __restrict__ ph,
+__global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __restrict__ ph,
                           const T* __restrict__ sh, const T* __restrict__ s, const T* __restrict__ t,
-                          T* __restrict__ r, const T* __restrict__ rh, double* __restrict__ part, int64_t pstride) {
+                          T* __restrict__ r, const T* __restrict__ rh, double* __restrict__ part,
+                          unsigned int* counter) {
   if (sc[S_DONE] != 0.0) return;
   const T al = (T)sc[S_ALPHA], om = (T)sc[S_OMEGA];
   double acc[2] = {0.0, 0.0};
@@ -353,26 +397,16 @@ __global__ void k_bicg_xr(int64_t N, const double* __restrict__ sc, T* __restric
     acc[0] += (double)ri * (double)ri;
     acc[1] += (double)rh[i] * (double)ri;
   }
-  block_sums_to<2>(acc, part, pstride);
-}
-
-__global__ void k_bicg_fin_r(const double* __restrict__ part, int n, int64_t pstride, double* sc) {
-  if (sc[S_DONE] != 0.0) return;
-  double v0 = 0.0, v1 = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    v0 += part[q];
-    v1 += part[pstride + q];
-  }
-  double vv[2] = {v0, v1};
-  block_sums_to<2>(vv, sc + S_END, 1);
+  double tot[2];
+  if (!last_block_sums<2>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
-    const double nr = sqrt(sc[S_END]);
+    const double nr = sqrt(tot[0]);
     sc[S_NRES] = nr;
     sc[S_RHO_OLD] = sc[S_RHO];
-    sc[S_RHO] = sc[S_END + 1];
+    sc[S_RHO] = tot[1];
     sc[S_ITS] += 1.0;
     if (!isfinite(nr)) sc[S_DONE] = 2.0;
-    else if (nr < sc[S_TOL]) sc[S_DONE] = 1.0;
+    else if (stop_test(nr, sc)) sc[S_DONE] = 1.0;
     else if (sc[S_ITS] >= sc[S_MAXIT]) sc[S_DONE] = 4.0;
   }
 }
@@ -386,40 +420,35 @@ __global__ void k_to_double(int64_t N, const T* __restrict__ x, double* __restri
 // ---- GMRES(m), right Jacobi preconditioning, classical Gram-Schmidt with one
 // re-orthogonalisation pass ----
 
-// w = rhs - B x  (x = 0 on the first cycle), partial ||w||^2
-template <class T>
-__global__ void k_gm_residual(int64_t N, Offsets of, const double* __restrict__ sc, const T* __restrict__ B,
-                              const T* __restrict__ x, const double* __restrict__ rhs, T* __restrict__ w,
-                              double* __restrict__ part) {
+// w = rhs - B x (x = 0 on the first cycle) and ||w||; the last block runs the stop test
+// on this true residual and starts a cycle: g = (beta, 0, ...), invh = 1 / beta
+template <int KT, class T>
+__global__ void k_gm_residual(int64_t N, Offsets of, double* sc, const T* __restrict__ B, const T* __restrict__ x,
+                              const double* __restrict__ rhs, T* __restrict__ w, double* __restrict__ part,
+                              unsigned int* counter) {
   if (sc[S_DONE] != 0.0) return;
+  const int K = KT > 0 ? KT : of.K;
+  const bool first = sc[S_FIRST] != 0.0;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double acc = 0.0;
+  double acc[1] = {0.0};
   if (i < N) {
     T s = 0;
-    if (sc[S_FIRST] == 0.0) {
-#pragma unroll 4
-      for (int k = 0; k < of.K; ++k) s = fma(B[k * N + i], x[i + of.o[k]], s);
+    if (!first) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s = fma(B[k * N + i], x[i + of.o[k]], s);
     }
     const T wi = (T)rhs[i] - s;
     w[i] = wi;
-    acc = (double)wi * (double)wi;
+    acc[0] = (double)wi * (double)wi;
   }
-  block_sum_to(acc, part);
-}
-
-// beta = ||r||; stop test on the true residual; start a new cycle
-__global__ void k_gm_start(const double* __restrict__ part, int n, double* sc, double atol, double rtol, int maxit) {
-  if (sc[S_DONE] != 0.0) return;
-  double v = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) v += part[q];
-  block_sum_to(v, sc + S_END);
+  double tot[1];
+  if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
-    const double beta = sqrt(sc[S_END]);
-    if (sc[S_FIRST] != 0.0) {
+    const double beta = sqrt(tot[0]);
+    if (first) {
       sc[S_N0] = beta;
-      sc[S_TOL] = fmax(atol, rtol * beta);
+      sc[S_TOL] = fmax(sc[S_ATOL], sc[S_RTOL] * beta);
       sc[S_ITS] = 0.0;
-      sc[S_MAXIT] = (double)maxit;
       sc[S_FIRST] = 0.0;
     }
     sc[S_NRES] = beta;
@@ -427,7 +456,7 @@ __global__ void k_gm_start(const double* __restrict__ part, int n, double* sc, d
     sc[S_K_USED] = 0.0;
     sc[S_CYCLE_DONE] = 0.0;
     if (!isfinite(beta)) sc[S_DONE] = 2.0;
-    else if (beta < sc[S_TOL]) sc[S_DONE] = 1.0;
+    else if (stop_test(beta, sc)) sc[S_DONE] = 1.0;
     else if (sc[S_ITS] >= sc[S_MAXIT]) sc[S_DONE] = 4.0;
     for (int q = 0; q <= kMaxRestart; ++q) sc[S_G + q] = 0.0;
     sc[S_G] = beta;
@@ -435,7 +464,7 @@ __global__ void k_gm_start(const double* __restrict__ part, int n, double* sc, d
   }
 }
 
-// v_k = w * invh; z = dinv * v_k
+// v_k = w * invh; z = D^{-1} v_k
 template <class T>
 __global__ void k_gm_normalize(int64_t N, const double* __restrict__ sc, const T* __restrict__ w, T* __restrict__ vk,
                                const T* __restrict__ dinv, T* __restrict__ z) {
@@ -448,24 +477,30 @@ __global__ void k_gm_normalize(int64_t N, const double* __restrict__ sc, const T
   }
 }
 
-template <class T>
+template <int KT, class T>
 __global__ void k_gm_spmv(int64_t N, Offsets of, const double* __restrict__ sc, const T* __restrict__ B,
                           const T* __restrict__ z, T* __restrict__ w) {
   if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
+  const int K = KT > 0 ? KT : of.K;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   T s = 0;
-#pragma unroll 4
-  for (int k = 0; k < of.K; ++k) s = fma(B[k * N + i], z[i + of.o[k]], s);
+#pragma unroll
+  for (int k = 0; k < K; ++k) s = fma(B[k * N + i], z[i + of.o[k]], s);
   w[i] = s;
 }
 
-// optionally w -= sum_q h[q] V_q (h from sc + hslot), then partials of (w, V_q), q <= k
+// Gram-Schmidt pass: optionally w -= sum_q h[q] V_q (h at sc + hslot), then the dots
+// (w, V_q), q <= k (pass 1, 2) or ||w|| (pass 3).  The last block stores the dots at
+// sc + outslot (passes 1, 2) or completes Hessenberg column k (pass 3): H[0..k][k] =
+// h1 + h2, H[k+1][k] = ||w||, earlier Givens rotations, a new rotation, the residual
+// estimate |g[k+1]|, the end-of-cycle test and invh = 1 / ||w||.
 template <class T>
-__global__ void k_gm_orth(int64_t N, const double* __restrict__ sc, int k, int hslot, T* __restrict__ w,
+__global__ void k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int outslot, T* __restrict__ w,
                           const T* __restrict__ V, size_t vstride, double* __restrict__ part, int64_t pstride,
-                          int want_norm) {
+                          unsigned int* counter) {
   if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
+  const bool want_norm = outslot < 0;
   __shared__ double hs[kMaxRestart + 1];
   for (int q = threadIdx.x; q <= k; q += blockDim.x) hs[q] = hslot >= 0 ? sc[hslot + q] : 0.0;
   __syncthreads();
@@ -484,10 +519,9 @@ __global__ void k_gm_orth(int64_t N, const double* __restrict__ sc, int k, int h
       for (int q = 0; q <= k; ++q) acc[q] += (double)wi * (double)V[q * vstride + i];
     }
   }
-  // block reduction of k+1 (or 1) values
+  const int nq = want_norm ? 1 : k + 1;
   __shared__ double red[kBlock / 32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int nq = want_norm ? 1 : k + 1;
   for (int q = 0; q < nq; ++q) {
     double t = warp_sum(want_norm ? nrm : acc[q]);
     if (lane == 0) red[wp] = t;
@@ -499,28 +533,25 @@ __global__ void k_gm_orth(int64_t N, const double* __restrict__ sc, int k, int h
     }
     __syncthreads();
   }
-}
-
-// h[q] = sum of the partials of dot q, stored at sc + hslot + q
-__global__ void k_gm_fin_dots(const double* __restrict__ part, int n, int64_t pstride, int nq, double* sc, int hslot) {
-  if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
-  for (int q = 0; q < nq; ++q) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[q * pstride + b];
-    block_sum_to(v, sc + S_END);
-    if (threadIdx.x == 0) sc[hslot + q] = sc[S_END];
-    __syncthreads();
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
-}
-
-// Hessenberg column k = h1 + h2, subdiagonal = ||w||; Givens rotations; residual estimate
-__global__ void k_gm_column(const double* __restrict__ part, int n, double* sc, int k, int m) {
-  if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
-  double v = 0.0;
-  for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
-  block_sum_to(v, sc + S_END);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double last = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + q * pstride + b);
+    last = block_allsum(s);
+    if (!want_norm && threadIdx.x == 0) sc[outslot + q] = last;
+  }
   if (threadIdx.x != 0) return;
-  const double hk1 = sqrt(sc[S_END]);
+  *counter = 0u;
+  if (!want_norm) return;
+  const double hk1 = sqrt(last);
   double* H = sc + S_HCOL;   // H[row * kMaxRestart + col]
   for (int q = 0; q <= k; ++q) H[q * kMaxRestart + k] = sc[S_H1 + q] + sc[S_H2 + q];
   H[(k + 1) * kMaxRestart + k] = hk1;
@@ -545,23 +576,11 @@ __global__ void k_gm_column(const double* __restrict__ part, int n, double* sc, 
   sc[S_NRES] = fabs(g[k + 1]);
   sc[S_INVH] = 1.0 / hk1;
   if (!isfinite(den) || den == 0.0) { sc[S_DONE] = 2.0; return; }
-  if (fabs(g[k + 1]) < sc[S_TOL] || sc[S_ITS] >= sc[S_MAXIT] || k + 1 == m || hk1 == 0.0) sc[S_CYCLE_DONE] = 1.0;
+  if (stop_test(fabs(g[k + 1]), sc) || sc[S_ITS] >= sc[S_MAXIT] || k + 1 == m || hk1 == 0.0) sc[S_CYCLE_DONE] = 1.0;
 }
 
-// back substitution H y = g for the k_used leading columns
-__global__ void k_gm_solve(double* sc) {
-  if (threadIdx.x != 0 || sc[S_DONE] == 2.0) return;
-  const int ku = (int)sc[S_K_USED];
-  const double* H = sc + S_HCOL;
-  double* y = sc + S_Y;
-  for (int q = ku - 1; q >= 0; --q) {
-    double s = sc[S_G + q];
-    for (int c = q + 1; c < ku; ++c) s -= H[q * kMaxRestart + c] * y[c];
-    y[q] = s / H[q * kMaxRestart + q];
-  }
-}
-
-// x += dinv * sum_q y_q V_q
+// back substitution H y = g for the k_used leading columns, then x += D^{-1} sum_q y_q V_q
+// (every block solves the small triangular system itself)
 template <class T>
 __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restrict__ x, const T* __restrict__ V,
                             size_t vstride, const T* __restrict__ dinv) {
@@ -569,7 +588,14 @@ __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restr
   const int ku = (int)sc[S_K_USED];
   if (ku == 0) return;
   __shared__ double ys[kMaxRestart];
-  for (int q = threadIdx.x; q < ku; q += blockDim.x) ys[q] = sc[S_Y + q];
+  if (threadIdx.x == 0) {
+    const double* H = sc + S_HCOL;
+    for (int q = ku - 1; q >= 0; --q) {
+      double s = sc[S_G + q];
+      for (int c = q + 1; c < ku; ++c) s -= H[q * kMaxRestart + c] * ys[c];
+      ys[q] = s / H[q * kMaxRestart + q];
+    }
+  }
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     T s = 0;
@@ -578,11 +604,15 @@ __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restr
   }
 }
 
-__global__ void k_gm_reset(double* sc) {
+__global__ void k_solver_reset(double* sc, double atol, double rtol, int maxit) {
   if (threadIdx.x == 0) {
     sc[S_DONE] = 0.0;
     sc[S_FIRST] = 1.0;
     sc[S_K_USED] = 0.0;
+    sc[S_CYCLE_DONE] = 0.0;
+    sc[S_ATOL] = atol;
+    sc[S_RTOL] = rtol;
+    sc[S_MAXIT] = (double)maxit;
   }
 }
 
@@ -593,6 +623,7 @@ void krylov_free(afc_problem_s* p) {
   p->kw->vec.free_();
   p->kw->sc.free_();
   p->kw->part.free_();
+  p->kw->counter.free_();
   if (p->kw->hsc) cudaFreeHost(p->kw->hsc);
   delete p->kw;
   p->kw = nullptr;
@@ -620,12 +651,13 @@ int ensure_work(afc_problem_s* p, int nvec, bool fp32) {
   if (!w.sc.base) {
     int st = w.sc.alloc(S_END + 8);
     if (st) return st;
+    if ((st = w.counter.alloc(4))) return st;
     if (cudaMallocHost((void**)&w.hsc, (S_END + 8) * sizeof(double)) != cudaSuccess) {
       set_error("cudaMallocHost failed");
       return AFC_E_OOM;
     }
   }
-  const int64_t need_part = (int64_t)(kMaxRestart + 2) * std::max<int64_t>(kRedBlocks, grid_for(p->N));
+  const int64_t need_part = (int64_t)(kMaxRestart + 4) * std::max<int64_t>(kRedBlocks, grid_for(p->N));
   if (w.part.n < need_part) {
     int st = w.part.alloc(need_part);
     if (st) return st;
@@ -650,11 +682,11 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
     *sv = vec_at<T>(w, 5), *t = vec_at<T>(w, 6), *ph = vec_at<T>(w, 7), *sh = vec_at<T>(w, 8);
   double* sc = w.sc.p;
   double* part = w.part.p;
+  unsigned int* cnt = w.counter.p;
   const int G = kRedBlocks;
   const int64_t gr = grid_for(N);
-  const int64_t pst = std::max<int64_t>(G, gr);
-  AFC_LAUNCH(p, "k_bicg_init", k_bicg_init<T><<<G, kBlock, 0, s>>>(N, rhs, x, r, rh, pp, v, part));
-  AFC_LAUNCH(p, "k_bicg_init_fin", k_bicg_init_fin<<<1, 1024, 0, s>>>(part, G, sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
+  AFC_LAUNCH(p, "k_solver_reset", k_solver_reset<<<1, 32, 0, s>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
+  AFC_LAUNCH(p, "k_bicg_init", k_bicg_init<T><<<G, kBlock, 0, s>>>(N, rhs, x, r, rh, pp, v, part, cnt, sc));
   AFC_CUDA(cudaGetLastError());
   int chunk = 2;
   int launched = 0;
@@ -662,18 +694,18 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
     AFC_CUDA(cudaMemcpyAsync(w.hsc, sc, (S_MAXIT + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFC_CUDA(cudaStreamSynchronize(s));
     if (w.hsc[S_DONE] != 0.0 || launched >= o->ksp_maxit) break;
-    for (int c = 0; c < chunk && launched < o->ksp_maxit; ++c, ++launched) {
-      AFC_LAUNCH(p, "k_bicg_p", k_bicg_p<T><<<G, kBlock, 0, s>>>(N, sc, r, pp, v, dinv, ph));
-      AFC_LAUNCH(p, "k_bicg_spmv", k_bicg_spmv<T, 1><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, ph, v, rh, part, pst));
-      AFC_LAUNCH(p, "k_bicg_fin_alpha", k_bicg_fin_alpha<<<1, 1024, 0, s>>>(part, (int)gr, sc));
-      AFC_LAUNCH(p, "k_bicg_s", k_bicg_s<T><<<G, kBlock, 0, s>>>(N, sc, r, v, dinv, sv, sh, part));
-      AFC_LAUNCH(p, "k_bicg_fin_s", k_bicg_fin_s<<<1, 1024, 0, s>>>(part, G, sc));
-      AFC_LAUNCH(p, "k_bicg_early_x", k_bicg_early_x<T><<<G, kBlock, 0, s>>>(N, sc, x, ph));
-      AFC_LAUNCH(p, "k_bicg_spmv", k_bicg_spmv<T, 2><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, sh, t, sv, part, pst));
-      AFC_LAUNCH(p, "k_bicg_fin_omega", k_bicg_fin_omega<<<1, 1024, 0, s>>>(part, (int)gr, pst, sc));
-      AFC_LAUNCH(p, "k_bicg_xr", k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, pst));
-      AFC_LAUNCH(p, "k_bicg_fin_r", k_bicg_fin_r<<<1, 1024, 0, s>>>(part, G, pst, sc));
-    }
+    with_K(p->K, [&](auto kc) {
+      constexpr int KT = decltype(kc)::value;
+      for (int c = 0; c < chunk && launched < o->ksp_maxit; ++c, ++launched) {
+        AFC_LAUNCH(p, "k_bicg_p", k_bicg_p<T><<<G, kBlock, 0, s>>>(N, sc, r, pp, v, dinv, ph));
+        AFC_LAUNCH(p, "k_bicg_spmv1",
+                   k_bicg_spmv1<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, ph, v, rh, part, cnt));
+        AFC_LAUNCH(p, "k_bicg_s", k_bicg_s<T><<<G, kBlock, 0, s>>>(N, sc, r, v, dinv, sv, sh, part, cnt));
+        AFC_LAUNCH(p, "k_bicg_spmv2",
+                   k_bicg_spmv2<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, sh, t, sv, x, ph, part, cnt));
+        AFC_LAUNCH(p, "k_bicg_xr", k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, cnt));
+      }
+    });
     AFC_CUDA(cudaGetLastError());
     chunk = std::min(chunk * 2, 16);
   }
@@ -701,31 +733,32 @@ int gmres_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, c
   const size_t vs = w.vstride;
   double* sc = w.sc.p;
   double* part = w.part.p;
+  unsigned int* cnt = w.counter.p;
   const int G = kRedBlocks;
   const int64_t gr = grid_for(N);
-  const int64_t pst = std::max<int64_t>(G, gr);
   AFC_CUDA(cudaMemsetAsync(x - p->pad, 0, vs * sizeof(T), s));
-  AFC_LAUNCH(p, "k_gm_reset", k_gm_reset<<<1, 32, 0, s>>>(sc));
+  AFC_LAUNCH(p, "k_solver_reset", k_solver_reset<<<1, 32, 0, s>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
   for (;;) {
-    // true residual, stop test, new cycle
-    AFC_LAUNCH(p, "k_gm_residual", k_gm_residual<T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, x, rhs, wv, part));
-    AFC_LAUNCH(p, "k_gm_start", k_gm_start<<<1, 1024, 0, s>>>(part, (int)gr, sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
+    with_K(p->K, [&](auto kc) {
+      constexpr int KT = decltype(kc)::value;
+      AFC_LAUNCH(p, "k_gm_residual",
+                 k_gm_residual<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, x, rhs, wv, part, cnt));
+    });
     AFC_CUDA(cudaGetLastError());
     AFC_CUDA(cudaMemcpyAsync(w.hsc, sc, S_CS * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFC_CUDA(cudaStreamSynchronize(s));
     if (w.hsc[S_DONE] != 0.0) break;
     AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V, dinv, z));
     for (int k = 0; k < m; ++k) {
-      AFC_LAUNCH(p, "k_gm_spmv", k_gm_spmv<T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv));
-      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, -1, wv, V, vs, part, G, 0));
-      AFC_LAUNCH(p, "k_gm_fin_dots", k_gm_fin_dots<<<1, 1024, 0, s>>>(part, G, G, k + 1, sc, S_H1));
-      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, S_H1, wv, V, vs, part, G, 0));
-      AFC_LAUNCH(p, "k_gm_fin_dots", k_gm_fin_dots<<<1, 1024, 0, s>>>(part, G, G, k + 1, sc, S_H2));
-      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, S_H2, wv, V, vs, part, G, 1));
-      AFC_LAUNCH(p, "k_gm_column", k_gm_column<<<1, 1024, 0, s>>>(part, G, sc, k, m));
+      with_K(p->K, [&](auto kc) {
+        constexpr int KT = decltype(kc)::value;
+        AFC_LAUNCH(p, "k_gm_spmv", k_gm_spmv<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv));
+      });
+      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, -1, S_H1, wv, V, vs, part, G, cnt));
+      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H1, S_H2, wv, V, vs, part, G, cnt));
+      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt));
       AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z));
     }
-    AFC_LAUNCH(p, "k_gm_solve", k_gm_solve<<<1, 32, 0, s>>>(sc));
     AFC_LAUNCH(p, "k_gm_update", k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv));
     AFC_CUDA(cudaGetLastError());
   }
