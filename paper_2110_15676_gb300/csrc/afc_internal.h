@@ -119,6 +119,10 @@ struct afc_problem_s {
   afc::DBuf<double> Mfull, Sfull, Kfull, Afull;   // K * N each
   afc::DBuf<double> AA;                           // K * N, low-order operator
   afc::DBuf<double> m_up, d_up;                   // Kup * N, symmetric edge data
+  afc::DBuf<double> kij_up, kji_up;               // Kup * N, MC: convective k_ij and k_ji of each pair i < j
+  afc::DBuf<double> d2_up;                        // Kup * N, MC: 2 |d_ij|
+  afc::DBuf<float> pairf;                         // 3 * Kup * N, MC: 2|d_ij|, k_ij, k_ji rounded to single
+  afc::DBuf<double> AG;                           // K * N, MC: unlimited operator K + eps S + c M_L
   afc::DBuf<double> mL, f;                        // N
   afc::DBuf<double> Bst;                          // K * N, stationary system (Dirichlet rows = identity)
   afc::DBuf<float> Bst32;
@@ -134,6 +138,9 @@ struct afc_problem_s {
 
   // state and work vectors (node vectors carry the halo)
   afc::DBuf<double> u, u0, ustage, udot, ut, Rp, Rm, Fs, Qp, Qm, b0, res, delta, umax, umin, tmp, cn_a, cn_s;
+  afc::DBuf<double> bA, bB;         // MC: u_max - u and u - u_min
+  afc::DBuf<unsigned int> clip;     // MC: per row, bit ku set if the pair (i, i + o) was clipped
+  afc::DBuf<float4> nodef;          // MC: (u, u_max - u, u - u_min) rounded to single
   afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
   afc::DBuf<double> scal;           // small device scalars (norms, dt, ...)
   afc::DBuf<double> part;           // reduction partials
@@ -162,7 +169,8 @@ int cn_update(afc_problem_s* p, double omega, const double* delta, double* u, co
 int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int limiter, int prelimit, double* res,
                         double* normsq_slot);                                      // needs cn_update first
 // MC
-int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot);
+int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot,
+                        bool want_F = false);
 
 // ---- reductions and BLAS-1 (krylov.cu) ----
 int dot_device(afc_problem_s* p, const double* x, const double* y, double* out_slot);

@@ -81,7 +81,7 @@ int create_common(afc_problem_s* p) {
     return st;
   DBuf<double>* vecs[] = {&p->u,  &p->u0,  &p->ustage, &p->udot, &p->ut,   &p->Rp,  &p->Rm,
                           &p->Fs, &p->Qp,  &p->Qm,     &p->b0,   &p->res,  &p->delta, &p->umax,
-                          &p->umin, &p->tmp, &p->cn_a, &p->cn_s};
+                          &p->umin, &p->tmp, &p->cn_a, &p->cn_s, &p->bA, &p->bB};
   for (auto* v : vecs)
     if ((st = v->alloc(N, p->pad))) return st;
   if ((st = p->scal.alloc(64)) || (st = p->part.alloc(4 * std::max<int64_t>(kRedBlocks, grid_for(N))))) return st;
@@ -108,10 +108,12 @@ void destroy_all(afc_problem_s* p) {
                         &p->AA, &p->m_up, &p->d_up, &p->mL, &p->f, &p->Bst, &p->dinv_st, &p->Bcn, &p->dinv_cn,
                         &p->u, &p->u0, &p->ustage, &p->udot, &p->ut, &p->Rp, &p->Rm, &p->Fs, &p->Qp, &p->Qm,
                         &p->b0, &p->res, &p->delta, &p->umax, &p->umin, &p->tmp, &p->cn_a, &p->cn_s,
-                        &p->scal, &p->part, &p->r_up, &p->mdt_up, &p->mLdt};
+                        &p->scal, &p->part, &p->r_up, &p->mdt_up, &p->mLdt, &p->kij_up, &p->kji_up,
+                        &p->AG, &p->bA, &p->bB, &p->d2_up};
   for (auto* b : dv) b->free_();
   p->Bst32.free_(); p->dinv_st32.free_(); p->Bcn32.free_(); p->dinv_cn32.free_();
-  p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_();
+  p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_(); p->clip.free_();
+  p->pairf.free_(); p->nodef.free_();
   if (p->host_scal) cudaFreeHost(p->host_scal);
   delete p;
 }
@@ -459,7 +461,10 @@ int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
     set_error("afc_solve_stationary supports limiters NONE, GALERKIN, MC");
     return AFC_E_INVALID;
   }
-  if (lim == AFC_LIM_MC && p->family != AFC_FAMILY_MC) { set_error("MC limiter needs the MC family"); return AFC_E_STATE; }
+  if (lim != AFC_LIM_NONE && p->family != AFC_FAMILY_MC) {
+    set_error("the stationary MC limiter and its Galerkin mode need the MC family");
+    return AFC_E_STATE;
+  }
   AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
   st = fixed_point(
@@ -503,7 +508,11 @@ int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax
   if (st) return st;
   if (!u) { set_error("null argument"); return AFC_E_INVALID; }
   if ((st = to_device(p, p->ustage.p, u, p->N))) return st;
-  if ((st = mc_limited_residual(p, p->ustage.p, limiter, p->res.p, p->scal.p))) return st;
+  if (p->family != AFC_FAMILY_MC && limiter != AFC_LIM_NONE) {
+    set_error("the MC limiter and its Galerkin mode need afc_assemble(..., AFC_FAMILY_MC, ...)");
+    return AFC_E_STATE;
+  }
+  if ((st = mc_limited_residual(p, p->ustage.p, limiter, p->res.p, p->scal.p, true))) return st;
   if ((st = to_host(p, umax, p->umax.p, p->N)) || (st = to_host(p, umin, p->umin.p, p->N)) ||
       (st = to_host(p, Fstar, p->Fs.p, p->N)))
     return st;
@@ -517,6 +526,7 @@ int afc_mc_residual_sweep(afc_problem p, int limiter) {
     set_error("limiter must be NONE, GALERKIN or MC");
     return AFC_E_INVALID;
   }
+  if (p->family != AFC_FAMILY_MC && limiter != AFC_LIM_NONE) { set_error("needs the MC family"); return AFC_E_STATE; }
   return mc_limited_residual(p, p->u.p, limiter, p->res.p, p->scal.p);
 }
 

@@ -204,6 +204,34 @@ __global__ void k_low_order(int64_t N, Offsets of, int family, double eps, doubl
   AAf[of.Kup * N + i] = dv;
 }
 
+// MC family: the convective entries of each pair i < j at row i (k_ij, k_ji) and the
+// unlimited operator AG = K + eps S + c M_L (AA without D) of the residual.
+__global__ void k_mc_extras(int64_t N, Offsets of, double eps, double c, const unsigned long long* __restrict__ mask,
+                            const double* __restrict__ Kf, const double* __restrict__ Sf,
+                            const double* __restrict__ mL, const double* __restrict__ dup,
+                            double* __restrict__ kij, double* __restrict__ kji, double* __restrict__ d2,
+                            float* __restrict__ pairf, double* __restrict__ AG) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const unsigned long long mk = mask[i];
+  for (int ku = 0; ku < of.Kup; ++ku) {
+    const int k = of.Kup + 1 + ku;
+    const bool present = (mk >> k) & 1ull;
+    kij[ku * N + i] = present ? Kf[k * N + i] : 0.0;
+    kji[ku * N + i] = present ? Kf[(of.Kup - 1 - ku) * N + i + of.o[k]] : 0.0;
+    d2[ku * N + i] = -2.0 * dup[ku * N + i];
+    const int64_t KN = (int64_t)of.Kup * N;
+    pairf[ku * N + i] = (float)d2[ku * N + i];
+    pairf[KN + ku * N + i] = (float)kij[ku * N + i];
+    pairf[2 * KN + ku * N + i] = (float)kji[ku * N + i];
+  }
+  for (int k = 0; k < of.K; ++k) {
+    double v = Kf[k * N + i] + eps * Sf[k * N + i];
+    if (k == of.Kup) v = v + c * mL[i];
+    AG[k * N + i] = v;
+  }
+}
+
 // System matrix: scale * AA, plus m_i / dt on the diagonal if dt > 0; Dirichlet rows -> identity.
 template <class T>
 __global__ void k_system(int64_t N, Offsets of, const double* __restrict__ AAf, const double* __restrict__ mL,
@@ -251,6 +279,15 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
   AFC_LAUNCH(p, "k_upwind_edges", k_upwind_edges<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->Afull.p, p->d_up.p));
   AFC_LAUNCH(p, "k_low_order", k_low_order<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->mask.p, p->Afull.p, p->Sfull.p, p->mL.p,
                                    p->d_up.p, p->AA.p));
+  if (family == AFC_FAMILY_MC) {
+    if ((st = p->kij_up.alloc(Kup * N)) || (st = p->kji_up.alloc(Kup * N)) || (st = p->d2_up.alloc(Kup * N)) ||
+        (st = p->AG.alloc(K * N)) || (st = p->clip.alloc(N, p->pad)) || (st = p->pairf.alloc(3 * Kup * N)) ||
+        (st = p->nodef.alloc(N, p->pad)))
+      return st;
+    AFC_LAUNCH(p, "k_mc_extras", k_mc_extras<<<g, kBlock, 0, s>>>(N, p->offs, p->eps, p->c, p->mask.p, p->Kfull.p,
+                                                                   p->Sfull.p, p->mL.p, p->d_up.p, p->kij_up.p,
+                                                                   p->kji_up.p, p->d2_up.p, p->pairf.p, p->AG.p));
+  }
   // symmetric mass data of the upper half: m_up[ku][i] = m_{i, i + o}
   for (int ku = 0; ku < Kup; ++ku)
     AFC_CUDA(cudaMemcpyAsync(p->m_up.p + ku * N, p->Mfull.p + (Kup + 1 + ku) * N, N * sizeof(double),

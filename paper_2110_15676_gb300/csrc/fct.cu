@@ -44,20 +44,18 @@ __global__ void k_ssp_rate(int64_t N, Offsets of, const double* __restrict__ AA,
 
 // Eq. defn_r_ij_SSP for every pair i < j: r_ij = m_ij (udot_i - udot_j) + d_ij (u_j - u_i).
 // Pairs outside the pattern have m = d = 0 and get r = 0.
+// One thread per pair slot: block = 32 rows (threadIdx.x) x all upper offsets (threadIdx.y).
 template <int KT>
 __global__ void k_ssp_edges(int64_t N, Offsets of, const double* __restrict__ m_up, const double* __restrict__ d_up,
                             const double* __restrict__ u, const double* __restrict__ udot,
                             double* __restrict__ r_up) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int ku = threadIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
   if (i >= N) return;
-  const double ui = u[i], udi = udot[i];
-#pragma unroll
-  for (int ku = 0; ku < Kup; ++ku) {
-    const int64_t q = (int64_t)ku * N + i;
-    const int64_t j = i + of.o[Kup + 1 + ku];
-    r_up[q] = fma(m_up[q], udi - udot[j], d_up[q] * (u[j] - ui));
-  }
+  const int64_t q = (int64_t)ku * N + i;
+  const int64_t j = i + of.o[Kup + 1 + ku];
+  r_up[q] = fma(m_up[q], udot[i] - udot[j], d_up[q] * (u[j] - u[i]));
 }
 
 // Zalesak steps 1-3: P+/- from the stored fluxes, Q+/- from the predictor over N_i, R+/-.
@@ -72,18 +70,20 @@ __global__ void k_ssp_factors(int64_t N, Offsets of, const unsigned long long* _
   if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
   const unsigned long long mk = mask[i];
   const double uti = ut[i];
-  double Pp = 0.0, Pm = 0.0, tmax = uti, tmin = uti;
+  double Pp = 0.0, Pm = 0.0;
+  long long kmax = dkey(uti), kmin = kmax;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (k == Kup || !((mk >> k) & 1ull)) continue;
     const double r = pair_flux(of, Kup, k, i, N, r_up);
     if (gt0(r)) Pp += r;
     else if (!is0(r)) Pm += r;
-    const double utj = ut[i + of.o[k]];
-    tmax = imax(tmax, utj);
-    tmin = imin(tmin, utj);
+    const long long kj = dkey(ut[i + of.o[k]]);
+    kmax = kj > kmax ? kj : kmax;
+    kmin = kj < kmin ? kj : kmin;
   }
-  const double Qp = tmax - uti, Qm = tmin - uti;     // >= 0 and <= 0: the max/min include i itself
+  // >= 0 and <= 0: the max / min include i itself
+  const double Qp = from_key(kmax) - uti, Qm = from_key(kmin) - uti;
   const double m = mL[i];
   Rp[i] = zalesak_factor(m * Qp, dt * Pp);
   Rm[i] = zalesak_factor(m * Qm, dt * Pm);
@@ -158,16 +158,16 @@ __global__ void k_bounds_of(int64_t N, Offsets of, const unsigned long long* __r
   if (i >= N) return;
   const unsigned long long mk = mask[i];
   const double vi = v[i];
-  double tmax = vi, tmin = vi;
+  long long kmax = dkey(vi), kmin = kmax;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (!((mk >> k) & 1ull)) continue;
-    const double vj = v[i + of.o[k]];
-    tmax = imax(tmax, vj);
-    tmin = imin(tmin, vj);
+    const long long kj = dkey(v[i + of.o[k]]);
+    kmax = kj > kmax ? kj : kmax;
+    kmin = kj < kmin ? kj : kmin;
   }
-  Qp[i] = tmax - vi;
-  Qm[i] = tmin - vi;
+  Qp[i] = from_key(kmax) - vi;
+  Qm[i] = from_key(kmin) - vi;
 }
 
 // Node sums of the CN flux: a = u - u_old, s = u + u_old; optionally first
@@ -189,23 +189,21 @@ __global__ void k_cn_update(int64_t N, double omega, const double* __restrict__ 
 // Eq. flux_002 for every pair i < j, prelimited by Eq. prelimiting (L = 2) against twice
 // its diffusive part at the CN average:  q = d_ij (s_j - s_i) = 2 d_ij (ubar_j - ubar_i),
 // r = (m_ij / dt)(a_i - a_j) + q / 2,  r <- minmod(r, q).
+// One thread per pair slot: block = 32 rows (threadIdx.x) x all upper offsets (threadIdx.y).
 template <int KT>
 __global__ void k_cn_edges(int64_t N, Offsets of, const double* __restrict__ mdt_up, const double* __restrict__ d_up,
                            const double* __restrict__ a, const double* __restrict__ s, int prelimit,
                            double* __restrict__ r_up) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int ku = threadIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
   if (i >= N) return;
-  const double ai = a[i], si = s[i];
-#pragma unroll
-  for (int ku = 0; ku < Kup; ++ku) {
-    const int64_t q = (int64_t)ku * N + i;
-    const int64_t j = i + of.o[Kup + 1 + ku];
-    const double lim = d_up[q] * (s[j] - si);
-    double r = fma(mdt_up[q], ai - a[j], half_exact(lim));
-    if (prelimit) r = minmod(r, lim);
-    r_up[q] = r;
-  }
+  const int64_t q = (int64_t)ku * N + i;
+  const int64_t j = i + of.o[Kup + 1 + ku];
+  const double lim = d_up[q] * (s[j] - s[i]);
+  double r = fma(mdt_up[q], a[i] - a[j], half_exact(lim));
+  if (prelimit) r = minmod(r, lim);
+  r_up[q] = r;
 }
 
 // Zalesak steps 1-3 for the CN fluxes (Q+/- precomputed from the predictor).
@@ -289,7 +287,7 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
     AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, uin, p->f.p, p->mL.p,
                                                                      p->dir.p, p->udir.p, dt, p->udot.p, p->ut.p));
     if (limiter != AFC_LIM_NONE)
-      AFC_LAUNCH(p, "k_ssp_edges", k_ssp_edges<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->m_up.p, p->d_up.p, uin,
+      AFC_LAUNCH(p, "k_ssp_edges", k_ssp_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(N, p->offs, p->m_up.p, p->d_up.p, uin,
                                                                          p->udot.p, p->r_up.p));
     if (limiter == AFC_LIM_ZALESAK)
       AFC_LAUNCH(p, "k_ssp_factors", k_ssp_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->ut.p,
@@ -334,7 +332,7 @@ int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int li
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
     if (limiter != AFC_LIM_NONE)
-      AFC_LAUNCH(p, "k_cn_edges", k_cn_edges<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mdt_up.p, p->d_up.p, p->cn_a.p,
+      AFC_LAUNCH(p, "k_cn_edges", k_cn_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(N, p->offs, p->mdt_up.p, p->d_up.p, p->cn_a.p,
                                                                        p->cn_s.p, prelimit, p->r_up.p));
     if (limiter == AFC_LIM_ZALESAK)
       AFC_LAUNCH(p, "k_cn_factors", k_cn_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->Qp.p,

@@ -39,6 +39,17 @@ __device__ __forceinline__ bool lt0(double x) { return dkey(x) < -1; }          
 __device__ __forceinline__ bool is0(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ double imin(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }
 __device__ __forceinline__ double imax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+// keys are their own inverse: key(key(x)) = x
+__device__ __forceinline__ double from_key(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
 // min / max of two values known to be >= 0 (correction factors, bounds): plain int compare
 __device__ __forceinline__ double imin_nn(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
