@@ -94,6 +94,8 @@ typedef struct {
   int32_t gmres_restart;  /* GMRES(m) restart length, 1..64                               */
   int32_t precision;      /* afc_precision: AFC_MIXED runs the inner solve in FP32        */
   int32_t prelimit;       /* CN: apply Eq. prelimiting (L = 2)                            */
+  int32_t graph;          /* 1: run the whole step / solve as one CUDA graph with the     */
+                          /* loop control on the device (default); 0: host-driven loop    */
 } afc_opts;
 
 typedef struct {

@@ -45,7 +45,8 @@ class afc_opts(C.Structure):
     _fields_ = [("scheme", C.c_int32), ("limiter", C.c_int32), ("dt", C.c_double), ("fp_tol", C.c_double),
                 ("fp_maxit", C.c_int32), ("fp_fixed_its", C.c_int32), ("omega", C.c_double), ("ksp", C.c_int32),
                 ("ksp_maxit", C.c_int32), ("ksp_atol", C.c_double), ("ksp_rtol", C.c_double),
-                ("gmres_restart", C.c_int32), ("precision", C.c_int32), ("prelimit", C.c_int32)]
+                ("gmres_restart", C.c_int32), ("precision", C.c_int32), ("prelimit", C.c_int32),
+                ("graph", C.c_int32)]
 
 
 class afc_stats(C.Structure):

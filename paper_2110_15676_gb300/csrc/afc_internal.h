@@ -34,6 +34,12 @@ int cuda_fail(cudaError_t e, const char* what);
     if (e__ != cudaSuccess) return afc::cuda_fail(e__, #call); \
   } while (0)
 
+// A CUDA-graph condition a kernel may set (use = false outside graphs).
+struct GraphCond {
+  bool use = false;
+  cudaGraphConditionalHandle h = 0;
+};
+
 // Offsets passed by value to kernels (constant bank, unrolled loops).
 struct Offsets {
   int K;          // number of offsets (odd)
@@ -71,6 +77,7 @@ struct DBuf {
 
 struct KrylovWork;   // defined in krylov.cu
 struct Profiler;     // defined in prof.cpp
+struct StepGraph;    // defined in graph.cu
 
 }  // namespace afc
 
@@ -83,6 +90,7 @@ namespace afc {
 cudaEvent_t prof_start(afc_problem_s* p);
 void prof_stop(afc_problem_s* p, const char* name, cudaEvent_t start);
 void prof_free(afc_problem_s* p);
+bool prof_set_enabled(afc_problem_s* p, bool on);   // returns the previous state
 
 #define AFC_LAUNCH(p, name, ...)                       \
   do {                                                 \
@@ -148,6 +156,9 @@ struct afc_problem_s {
 
   afc::KrylovWork* kw = nullptr;
   afc::Profiler* prof = nullptr;
+  afc::StepGraph* g_step = nullptr;   // cached graph of afc_step
+  afc::StepGraph* g_stat = nullptr;   // cached graph of afc_solve_stationary
+  cudaStream_t cap_stream = nullptr;  // private stream used to capture graphs
   int64_t launches = 0;             // kernel launches issued on this problem
   int64_t device_bytes = 0;
 };
@@ -180,6 +191,13 @@ int dia_spmv(afc_problem_s* p, const double* A, const double* x, double* y);
 int axpy_device(afc_problem_s* p, double a, const double* x, double* y);   // y += a x
 int minmax_device(afc_problem_s* p, const double* x, double* mn, double* mx);
 void krylov_free(afc_problem_s* p);
+const void* krylov_key(afc_problem_s* p);   // changes when the solver workspace is reallocated
+
+// ---- whole steps as CUDA graphs (graph.cu) ----
+int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* st);
+int ssp_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* st);
+int stationary_graph(afc_problem_s* p, const afc_opts* o, afc_stats* st);
+void graph_free(afc_problem_s* p);
 
 int64_t grid_for(int64_t n, int block = kBlock);
 

@@ -102,6 +102,7 @@ void destroy_all(afc_problem_s* p) {
   if (!p) return;
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  graph_free(p);
   prof_free(p);
   krylov_free(p);
   DBuf<double>* dv[] = {&p->xyz, &p->bnod, &p->fnod, &p->udir, &p->Mfull, &p->Sfull, &p->Kfull, &p->Afull,
@@ -212,6 +213,7 @@ void afc_default_opts(afc_opts* o) {
   o->gmres_restart = 20;
   o->precision = AFC_FP64;
   o->prelimit = 1;
+  o->graph = 1;
 }
 
 static int create_with(afc_problem_s* p, int /*device*/, void* /*stream*/, afc_problem* out) {
@@ -422,6 +424,13 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
     return AFC_E_INVALID;
   }
   cudaStream_t s = p->stream;
+  const bool graph = o->graph != 0;   // captured on a private stream, launched on the problem's stream
+  if (graph && (o->scheme == AFC_SSP2 || o->scheme == AFC_SSP3)) return ssp_step_graph(p, o, stt);
+  if (graph && o->scheme == AFC_CN_NONLINEAR) {
+    if (p->family != AFC_FAMILY_FCT) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
+    if ((st = build_cn_system(p, o->dt))) return st;
+    return cn_step_graph(p, o, stt);
+  }
   AFC_CUDA(cudaMemcpyAsync(p->u0.p, p->u.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (o->scheme == AFC_SSP2) {
     if ((st = fe_stage(p, p->u0.p, o->dt, lim, 0.0, nullptr, 1.0, p->ustage.p))) return st;
@@ -465,6 +474,7 @@ int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
     set_error("the stationary MC limiter and its Galerkin mode need the MC family");
     return AFC_E_STATE;
   }
+  if (o->graph != 0) return stationary_graph(p, o, stt);
   AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
   st = fixed_point(

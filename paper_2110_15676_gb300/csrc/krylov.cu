@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "afc_internal.h"
+#include "graph_util.h"
 #include "kernels_common.cuh"
 
 namespace afc {
@@ -186,6 +187,9 @@ enum : int {
   S_END = S_HCOL + (kMaxRestart + 1) * kMaxRestart
 };
 // S_DONE: 0 running, 1 converged, 2 breakdown / non-finite, 3 converged at s (x update pending), 4 maxit
+static_assert(S_ITS == kKrylovItsSlot && S_DONE == kKrylovDoneSlot, "slot numbers shared with graph.cu");
+constexpr int S_CYCLES = 17;   // GMRES restart cycles begun (true-residual evaluations)
+static_assert(S_CYCLES < S_CS, "slot range");
 
 struct KrylovWork {
   int64_t N = 0;
@@ -387,8 +391,11 @@ template <class T>
 __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __restrict__ ph,
                           const T* __restrict__ sh, const T* __restrict__ s, const T* __restrict__ t,
                           T* __restrict__ r, const T* __restrict__ rh, double* __restrict__ part,
-                          unsigned int* counter) {
-  if (sc[S_DONE] != 0.0) return;
+                          unsigned int* counter, GraphCond cond) {
+  if (sc[S_DONE] != 0.0) {
+    if (cond.use && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond.h, 0u);
+    return;
+  }
   const T al = (T)sc[S_ALPHA], om = (T)sc[S_OMEGA];
   double acc[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -409,7 +416,13 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
     if (!isfinite(nr)) sc[S_DONE] = 2.0;
     else if (stop_test(nr, sc)) sc[S_DONE] = 1.0;
     else if (sc[S_ITS] >= sc[S_MAXIT]) sc[S_DONE] = 4.0;
+    if (cond.use) cudaGraphSetConditional(cond.h, sc[S_DONE] == 0.0 ? 1u : 0u);
   }
+}
+
+// arm a solver loop: condition = (solver still running)
+__global__ void k_cond_running(const double* __restrict__ sc, GraphCond cond) {
+  if (threadIdx.x == 0 && cond.use) cudaGraphSetConditional(cond.h, sc[S_DONE] == 0.0 ? 1u : 0u);
 }
 
 template <class T>
@@ -451,7 +464,9 @@ __global__ void k_gm_residual(int64_t N, Offsets of, double* sc, const T* __rest
       sc[S_TOL] = fmax(sc[S_ATOL], sc[S_RTOL] * beta);
       sc[S_ITS] = 0.0;
       sc[S_FIRST] = 0.0;
+      sc[S_CYCLES] = 0.0;
     }
+    sc[S_CYCLES] += 1.0;
     sc[S_NRES] = beta;
     sc[S_BETA] = beta;
     sc[S_K_USED] = 0.0;
@@ -584,7 +599,9 @@ __global__ void k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int ou
 // (every block solves the small triangular system itself)
 template <class T>
 __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restrict__ x, const T* __restrict__ V,
-                            size_t vstride, const T* __restrict__ dinv) {
+                            size_t vstride, const T* __restrict__ dinv, GraphCond cond) {
+  // another restart cycle only while the solve is running (set before any early return)
+  if (cond.use && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond.h, sc[S_DONE] == 0.0 ? 1u : 0u);
   if (sc[S_DONE] == 2.0) return;
   const int ku = (int)sc[S_K_USED];
   if (ku == 0) return;
@@ -704,7 +721,8 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
         AFC_LAUNCH(p, "k_bicg_s", k_bicg_s<T><<<G, kBlock, 0, s>>>(N, sc, r, v, dinv, sv, sh, part, cnt));
         AFC_LAUNCH(p, "k_bicg_spmv2",
                    k_bicg_spmv2<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, sh, t, sv, x, ph, part, cnt));
-        AFC_LAUNCH(p, "k_bicg_xr", k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, cnt));
+        AFC_LAUNCH(p, "k_bicg_xr", k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, cnt,
+                                                                     GraphCond{}));
       }
     });
     AFC_CUDA(cudaGetLastError());
@@ -760,7 +778,7 @@ int gmres_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, c
       AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt));
       AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z));
     }
-    AFC_LAUNCH(p, "k_gm_update", k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv));
+    AFC_LAUNCH(p, "k_gm_update", k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv, GraphCond{}));
     AFC_CUDA(cudaGetLastError());
   }
   AFC_LAUNCH(p, "k_to_double", k_to_double<T><<<G, kBlock, 0, s>>>(N, x, xout));
@@ -773,6 +791,153 @@ int gmres_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, c
 }
 
 }  // namespace
+
+namespace {
+
+template <class T>
+int bicgstab_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
+                   cudaStream_t cs, cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier) {
+  int st = ensure_work(p, 9, sizeof(T) == 4);
+  if (st) return st;
+  KrylovWork& w = *p->kw;
+  const int64_t N = p->N;
+  T *x = vec_at<T>(w, 0), *r = vec_at<T>(w, 1), *rh = vec_at<T>(w, 2), *pp = vec_at<T>(w, 3), *v = vec_at<T>(w, 4),
+    *sv = vec_at<T>(w, 5), *t = vec_at<T>(w, 6), *ph = vec_at<T>(w, 7), *sh = vec_at<T>(w, 8);
+  double* sc = w.sc.p;
+  double* part = w.part.p;
+  unsigned int* cnt = w.counter.p;
+  const int G = kRedBlocks;
+  const int64_t gr = grid_for(N);
+  GraphCond cond;
+  cond.use = true;
+  AFC_CUDA(cudaGraphConditionalHandleCreate(&cond.h, g, 0, 0));
+  if ((st = capture_into(p, cs, g, frontier, [&]() -> int {
+         AFC_LAUNCH(p, "k_solver_reset",
+                    k_solver_reset<<<1, 32, 0, p->stream>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
+         AFC_LAUNCH(p, "k_bicg_init", k_bicg_init<T><<<G, kBlock, 0, p->stream>>>(N, rhs, x, r, rh, pp, v, part, cnt, sc));
+         AFC_LAUNCH(p, "k_cond_running", k_cond_running<<<1, 32, 0, p->stream>>>(sc, cond));
+         AFC_CUDA(cudaGetLastError());
+         return AFC_OK;
+       }, frontier)))
+    return st;
+  cudaGraph_t body;
+  cudaGraphNode_t loop;
+  if ((st = add_conditional(g, frontier, cond.h, cudaGraphCondTypeWhile, &body, &loop))) return st;
+  std::vector<cudaGraphNode_t> inner;
+  if ((st = capture_into(p, cs, body, {}, [&]() -> int {
+         with_K(p->K, [&](auto kc) {
+           constexpr int KT = decltype(kc)::value;
+           cudaStream_t s = p->stream;
+           AFC_LAUNCH(p, "k_bicg_p", k_bicg_p<T><<<G, kBlock, 0, s>>>(N, sc, r, pp, v, dinv, ph));
+           AFC_LAUNCH(p, "k_bicg_spmv1",
+                      k_bicg_spmv1<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, ph, v, rh, part, cnt));
+           AFC_LAUNCH(p, "k_bicg_s", k_bicg_s<T><<<G, kBlock, 0, s>>>(N, sc, r, v, dinv, sv, sh, part, cnt));
+           AFC_LAUNCH(p, "k_bicg_spmv2",
+                      k_bicg_spmv2<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, sh, t, sv, x, ph, part, cnt));
+           AFC_LAUNCH(p, "k_bicg_xr",
+                      k_bicg_xr<T><<<G, kBlock, 0, s>>>(N, sc, x, ph, sh, sv, t, r, rh, part, cnt, cond));
+         });
+         AFC_CUDA(cudaGetLastError());
+         return AFC_OK;
+       }, inner)))
+    return st;
+  frontier.assign(1, loop);
+  return capture_into(p, cs, g, frontier, [&]() -> int {
+    AFC_LAUNCH(p, "k_to_double", k_to_double<T><<<G, kBlock, 0, p->stream>>>(N, x, xout));
+    AFC_CUDA(cudaGetLastError());
+    return AFC_OK;
+  }, frontier);
+}
+
+template <class T>
+int gmres_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
+                cudaStream_t cs, cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier) {
+  const int m = o->gmres_restart;
+  if (m < 1 || m > kMaxRestart) { set_error("gmres_restart must be in 1..64"); return AFC_E_INVALID; }
+  int st = ensure_work(p, 3 + m + 1, sizeof(T) == 4);
+  if (st) return st;
+  KrylovWork& w = *p->kw;
+  const int64_t N = p->N;
+  T *x = vec_at<T>(w, 0), *wv = vec_at<T>(w, 1), *z = vec_at<T>(w, 2), *V = vec_at<T>(w, 3);
+  const size_t vs = w.vstride;
+  double* sc = w.sc.p;
+  double* part = w.part.p;
+  unsigned int* cnt = w.counter.p;
+  const int G = kRedBlocks;
+  const int64_t gr = grid_for(N);
+  GraphCond cond;
+  cond.use = true;
+  AFC_CUDA(cudaGraphConditionalHandleCreate(&cond.h, g, 0, 0));
+  if ((st = capture_into(p, cs, g, frontier, [&]() -> int {
+         AFC_CUDA(cudaMemsetAsync(x - p->pad, 0, vs * sizeof(T), p->stream));
+         AFC_LAUNCH(p, "k_solver_reset",
+                    k_solver_reset<<<1, 32, 0, p->stream>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
+         AFC_LAUNCH(p, "k_cond_running", k_cond_running<<<1, 32, 0, p->stream>>>(sc, cond));
+         AFC_CUDA(cudaGetLastError());
+         return AFC_OK;
+       }, frontier)))
+    return st;
+  cudaGraph_t body;
+  cudaGraphNode_t loop;
+  if ((st = add_conditional(g, frontier, cond.h, cudaGraphCondTypeWhile, &body, &loop))) return st;
+  std::vector<cudaGraphNode_t> inner;
+  if ((st = capture_into(p, cs, body, {}, [&]() -> int {
+         cudaStream_t s = p->stream;
+         with_K(p->K, [&](auto kc) {
+           constexpr int KT = decltype(kc)::value;
+           AFC_LAUNCH(p, "k_gm_residual",
+                      k_gm_residual<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, x, rhs, wv, part, cnt));
+           AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V, dinv, z));
+           for (int k = 0; k < m; ++k) {
+             AFC_LAUNCH(p, "k_gm_spmv", k_gm_spmv<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv));
+             AFC_LAUNCH(p, "k_gm_orth",
+                        k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, -1, S_H1, wv, V, vs, part, G, cnt));
+             AFC_LAUNCH(p, "k_gm_orth",
+                        k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H1, S_H2, wv, V, vs, part, G, cnt));
+             AFC_LAUNCH(p, "k_gm_orth",
+                        k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt));
+             AFC_LAUNCH(p, "k_gm_normalize",
+                        k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z));
+           }
+           AFC_LAUNCH(p, "k_gm_update", k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv, cond));
+         });
+         AFC_CUDA(cudaGetLastError());
+         return AFC_OK;
+       }, inner)))
+    return st;
+  frontier.assign(1, loop);
+  return capture_into(p, cs, g, frontier, [&]() -> int {
+    AFC_LAUNCH(p, "k_to_double", k_to_double<T><<<G, kBlock, 0, p->stream>>>(N, x, xout));
+    AFC_CUDA(cudaGetLastError());
+    return AFC_OK;
+  }, frontier);
+}
+
+}  // namespace
+
+int krylov_graph(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, cudaStream_t cs,
+                 cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier) {
+  const bool mixed = o->precision == AFC_MIXED;
+  if (mixed && p->precision != AFC_MIXED) {
+    set_error("mixed-precision solve needs afc_assemble(..., AFC_MIXED)");
+    return AFC_E_STATE;
+  }
+  const bool gm = o->ksp == AFC_KSP_GMRES;
+  if (mixed) {
+    const float* B = system == 0 ? p->Bst32.p : p->Bcn32.p;
+    const float* di = system == 0 ? p->dinv_st32.p : p->dinv_cn32.p;
+    return gm ? gmres_graph<float>(p, B, di, o, rhs, x, cs, g, frontier)
+              : bicgstab_graph<float>(p, B, di, o, rhs, x, cs, g, frontier);
+  }
+  const double* B = system == 0 ? p->Bst.p : p->Bcn.p;
+  const double* di = system == 0 ? p->dinv_st.p : p->dinv_cn.p;
+  return gm ? gmres_graph<double>(p, B, di, o, rhs, x, cs, g, frontier)
+            : bicgstab_graph<double>(p, B, di, o, rhs, x, cs, g, frontier);
+}
+
+const double* krylov_scalars(afc_problem_s* p) { return p->kw ? p->kw->sc.p : nullptr; }
+int krylov_cycles_slot() { return S_CYCLES; }
+const void* krylov_key(afc_problem_s* p) { return p->kw ? (const void*)p->kw->vec.base : nullptr; }
 
 int krylov_solve(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, int* its,
                  double* res) {

@@ -58,6 +58,13 @@ void prof_stop(afc_problem_s* p, const char* name, cudaEvent_t start) {
   if (p->prof->pending.size() >= 100000) p->prof->drain();
 }
 
+bool prof_set_enabled(afc_problem_s* p, bool on) {
+  if (!p->prof) return false;
+  const bool was = p->prof->on;
+  p->prof->on = on;
+  return was;
+}
+
 void prof_free(afc_problem_s* p) {
   if (!p->prof) return;
   p->prof->drain();

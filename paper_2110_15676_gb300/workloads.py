@@ -125,3 +125,13 @@ def random_transient(rng: np.random.Generator, elem: str = Q1, n_range=(17, 49))
 
 def random_field(rng: np.random.Generator, N: int, lo=0.0, hi=1.0) -> np.ndarray:
     return rng.uniform(lo, hi, size=N)
+
+
+def front_field(xyz: np.ndarray, rng: np.random.Generator, width=0.03, noise=0.02) -> np.ndarray:
+    """A state with the structure limiters act on: a steep smooth front across a
+    randomly tilted plane, values in [0, 1], plus small seeded noise (local extrema)."""
+    nrm = rng.normal(size=3)
+    nrm /= np.linalg.norm(nrm)
+    s = (xyz - 0.5) @ nrm
+    base = 0.5 * (1.0 + np.tanh(s / width))
+    return np.clip(base + noise * rng.uniform(-1.0, 1.0, size=len(xyz)), 0.0, 1.0)

@@ -119,14 +119,16 @@ def test_fe_stage_pass_parity(afc, elem, n, limiter):
 
 
 @pytest.mark.parametrize("order", [2, 3])
-def test_ssp_rotating_run_parity_and_bounds(afc, order):
-    """The small rotating transient (Kuhn P1, 9^3 nodes, CFL 0.5, 20 steps)."""
+@pytest.mark.parametrize("graph", [1, 0])
+def test_ssp_rotating_run_parity_and_bounds(afc, order, graph):
+    """The small rotating transient (Kuhn P1, 9^3 nodes, CFL 0.5, 20 steps), as one CUDA
+    graph per step and as host-issued launches."""
     wl = W.rotating_transient("p1", 9)
     o, g = pair_from_workload(wl)
     dt = O.cfl_timestep(o, 0.5)
     u = wl.u0.copy()
     g.set_solution(u)
-    opts = afc.default_opts(scheme=afc.AFC_SSP2 if order == 2 else afc.AFC_SSP3, dt=dt)
+    opts = afc.default_opts(scheme=afc.AFC_SSP2 if order == 2 else afc.AFC_SSP3, dt=dt, graph=graph)
     for step in range(20):
         u = O.ssp_step(o, u, dt, order=order)
         st = g.step(opts)
@@ -180,7 +182,8 @@ def test_cn_limited_sum_parity(afc, elem, n, prelimit, limiter):
 
 @pytest.mark.parametrize("elem,n", [("q1", 9), ("p1", 8)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_cn_steps_parity(afc, elem, n, precision):
+@pytest.mark.parametrize("graph", [1, 0])
+def test_cn_steps_parity(afc, elem, n, precision, graph):
     """Nonlinear Zal+CN, CFL 1, a few steps; fixed number of corrections per step
     so that both sides do the same work, inner BiCGStab to 1e-14."""
     wl = W.rotating_transient(elem, n)
@@ -191,7 +194,7 @@ def test_cn_steps_parity(afc, elem, n, precision):
     mixed = precision == "mixed"
     opts = afc.default_opts(scheme=afc.AFC_CN_NONLINEAR, dt=dt, fp_fixed_its=6, ksp_atol=0.0 if mixed else 1e-14,
                             ksp_rtol=1e-6 if mixed else 0.0,
-                            precision=afc.AFC_MIXED if mixed else afc.AFC_FP64)
+                            precision=afc.AFC_MIXED if mixed else afc.AFC_FP64, graph=graph)
     for step in range(3):
         u, st_o = O.cn_step(o, u, dt, fixed_iterations=6, ksp_atol=1e-14)
         st = g.step(opts)
@@ -234,17 +237,32 @@ def test_mc_limited_sum_parity(afc, elem, n, limiter):
 
 
 @pytest.mark.parametrize("elem", ["p1", "q1"])
-def test_mc_stationary_parity(afc, elem):
+@pytest.mark.parametrize("graph", [1, 0])
+def test_mc_stationary_parity(afc, elem, graph):
     wl = W.stationary_inflow(elem, 9)
     o, g = pair_from_workload(wl, "mc")
     u_ref, st_o = O.mc_stationary(o, tol=1e-12, omega=0.5, ksp="gmres", ksp_atol=1e-14, max_outer=1000)
     g.set_solution(wl.u0)
     st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, fp_tol=1e-12, omega=0.5, ksp=afc.AFC_KSP_GMRES,
-                                             ksp_atol=1e-14, fp_maxit=1000))
+                                             ksp_atol=1e-14, fp_maxit=1000, graph=graph))
     assert st["status"] == afc.AFC_OK
     ug = g.get_solution()
     assert relerr(ug, u_ref) < STEP_TOL
     assert ug.min() >= -1e-10 and ug.max() <= 1 + 1e-10
+
+
+def test_stationary_bicgstab_and_not_converged_status(afc):
+    wl = W.stationary_inflow("p1", 9)
+    o, g = pair_from_workload(wl, "mc")
+    u_ref, _ = O.mc_stationary(o, tol=1e-11, omega=0.5, ksp="bicgstab", ksp_atol=1e-14, max_outer=1000)
+    g.set_solution(wl.u0)
+    st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, fp_tol=1e-11, omega=0.5, ksp=afc.AFC_KSP_BICGSTAB,
+                                             ksp_atol=1e-14, fp_maxit=1000))
+    assert st["status"] == afc.AFC_OK and relerr(g.get_solution(), u_ref) < STEP_TOL
+    # an iteration limit that is too small returns the last iterate with AFC_NOT_CONVERGED
+    g.set_solution(wl.u0)
+    st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, fp_tol=1e-11, omega=0.5, fp_maxit=3))
+    assert st["status"] == afc.AFC_NOT_CONVERGED and st["outer_its"] == 3
 
 
 @pytest.mark.parametrize("elem", ["p1", "q1"])
