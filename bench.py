@@ -202,6 +202,23 @@ def mc_sweep(afc, W, torch, flush, stream, reps):
     prof, _ = P.profile_read()
     P.profile(False)
     sweep_ms = ms / reps
+    # the whole stationary MC solve of this workload (damped fixed point, omega = 0.5,
+    # tol 1e-10, mixed-precision Jacobi-GMRES(20) inner solves to a relative 1e-6)
+    sopts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0, ksp_rtol=1e-6,
+                             fp_tol=1e-10, fp_maxit=1000, precision=afc.AFC_MIXED)
+    P.set_solution(wl.u0)
+    P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
+                                        ksp_rtol=1e-6, fp_fixed_its=1, precision=afc.AFC_MIXED))   # build / warm
+    P.set_solution(wl.u0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sst = P.solve_stationary(sopts)
+    e1.record(stream)
+    e1.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    u_sol = P.get_solution()
     # algorithmic work of one sweep (design notes): FP64 flops 14 per pair + 2 per entry;
     # bytes of the CSR count 4(N+1) + 12 nnz + 24 E + 24 N
     flops = 14.0 * E + 2.0 * nnz
@@ -215,7 +232,12 @@ def mc_sweep(afc, W, torch, flush, stream, reps):
            "alu": {"bound": "alu", "achieved": flops / (sweep_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                    "unit": "TFLOP/s", "frac": flops / (sweep_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                    "algorithmic_flops": flops},
-           "kernels": {k: {"ms": v[0] / reps, "launches": v[1] // reps} for k, v in prof.items()}}
+           "kernels": {k: {"ms": v[0] / reps, "launches": v[1] // reps} for k, v in prof.items()},
+           "solve": {"ms": solve_ms, "fixed_point_its": sst["outer_its"], "gmres_its": sst["inner_its"],
+                     "status": sst["status"], "res_final": sst["res_final"],
+                     "dof_iters_per_s": N * sst["outer_its"] / (solve_ms / 1e3),
+                     "umin": float(u_sol.min()), "umax": float(u_sol.max()),
+                     "options": "omega 0.5, tol 1e-10, mixed: FP32 Jacobi-GMRES(20) rtol 1e-6, FP64 outer"}}
     del P
     return out
 

@@ -176,7 +176,8 @@ int dia_spmv(afc_problem_s* p, const double* A, const double* x, double* y) {
 // ---------------------------------------------------------------------------
 // Solver workspace
 // ---------------------------------------------------------------------------
-constexpr int kMaxRestart = 64;
+constexpr int kMaxRestart = 32;   // GMRES(m), m <= 32: the Gram-Schmidt kernel keeps m dots in registers
+constexpr int kOrthQ = kMaxRestart;
 
 // device scalar slots
 enum : int {
@@ -262,7 +263,7 @@ __device__ __forceinline__ bool stop_test(double nr, const double* sc) { return 
 template <class T>
 __global__ void k_bicg_init(int64_t N, const double* __restrict__ rhs, T* x, T* r, T* rh, T* p, T* v,
                             double* __restrict__ part, unsigned int* counter, double* sc) {
-  double acc[1] = {0.0};
+  T a0 = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = (T)rhs[i];
     x[i] = 0;
@@ -270,8 +271,9 @@ __global__ void k_bicg_init(int64_t N, const double* __restrict__ rhs, T* x, T* 
     rh[i] = ri;
     p[i] = 0;
     v[i] = 0;
-    acc[0] += (double)ri * (double)ri;
+    a0 = fma(ri, ri, a0);
   }
+  double acc[1] = {(double)a0};
   double tot[1];
   if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
@@ -282,6 +284,7 @@ __global__ void k_bicg_init(int64_t N, const double* __restrict__ rhs, T* x, T* 
     sc[S_RHO_OLD] = 1.0;
     sc[S_ALPHA] = 1.0;
     sc[S_OMEGA] = 1.0;
+    sc[S_BETA] = (tot[0] / 1.0) * (1.0 / 1.0);
     sc[S_TOL] = fmax(sc[S_ATOL], sc[S_RTOL] * n0);
     sc[S_ITS] = 0.0;
     sc[S_DONE] = !isfinite(n0) ? 2.0 : (n0 < sc[S_TOL] ? 1.0 : (sc[S_MAXIT] <= 0.0 ? 4.0 : 0.0));
@@ -293,7 +296,7 @@ template <class T>
 __global__ void k_bicg_p(int64_t N, const double* __restrict__ sc, const T* __restrict__ r, T* p,
                          const T* __restrict__ v, const T* __restrict__ dinv, T* __restrict__ ph) {
   if (sc[S_DONE] != 0.0) return;
-  const T beta = (T)((sc[S_RHO] / sc[S_RHO_OLD]) * (sc[S_ALPHA] / sc[S_OMEGA]));
+  const T beta = (T)sc[S_BETA];       // (rho / rho_old)(alpha / omega), formed once by the previous kernel
   const T om = (T)sc[S_OMEGA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const T pi = r[i] + beta * (p[i] - om * v[i]);
@@ -316,7 +319,7 @@ __global__ void k_bicg_spmv1(int64_t N, Offsets of, double* sc, const T* __restr
 #pragma unroll
     for (int k = 0; k < K; ++k) s = fma(B[k * N + i], x[i + of.o[k]], s);
     y[i] = s;
-    acc[0] = (double)a[i] * (double)s;
+    acc[0] = (double)(a[i] * s);
   }
   double tot[1];
   if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
@@ -334,13 +337,14 @@ __global__ void k_bicg_s(int64_t N, double* sc, const T* __restrict__ r, const T
                          unsigned int* counter) {
   if (sc[S_DONE] != 0.0) return;
   const T al = (T)sc[S_ALPHA];
-  double acc[1] = {0.0};
+  T a0 = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const T si = r[i] - al * v[i];
     s[i] = si;
     sh[i] = dinv[i] * si;
-    acc[0] += (double)si * (double)si;
+    a0 = fma(si, si, a0);
   }
+  double acc[1] = {(double)a0};
   double tot[1];
   if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
@@ -372,8 +376,8 @@ __global__ void k_bicg_spmv2(int64_t N, Offsets of, double* sc, const T* __restr
 #pragma unroll
     for (int k = 0; k < K; ++k) v = fma(B[k * N + i], sh[i + of.o[k]], v);
     t[i] = v;
-    acc[0] = (double)v * (double)s[i];
-    acc[1] = (double)v * (double)v;
+    acc[0] = (double)(v * s[i]);
+    acc[1] = (double)(v * v);
   }
   double tot[2];
   if (!last_block_sums<2>(acc, part, gridDim.x, counter, tot)) return;
@@ -397,14 +401,15 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
     return;
   }
   const T al = (T)sc[S_ALPHA], om = (T)sc[S_OMEGA];
-  double acc[2] = {0.0, 0.0};
+  T a0 = 0, a1 = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = x[i] + al * ph[i] + om * sh[i];
     const T ri = s[i] - om * t[i];
     r[i] = ri;
-    acc[0] += (double)ri * (double)ri;
-    acc[1] += (double)rh[i] * (double)ri;
+    a0 = fma(ri, ri, a0);
+    a1 = fma(rh[i], ri, a1);
   }
+  double acc[2] = {(double)a0, (double)a1};
   double tot[2];
   if (!last_block_sums<2>(acc, part, gridDim.x, counter, tot)) return;
   if (threadIdx.x == 0) {
@@ -412,6 +417,7 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
     sc[S_NRES] = nr;
     sc[S_RHO_OLD] = sc[S_RHO];
     sc[S_RHO] = tot[1];
+    sc[S_BETA] = (sc[S_RHO] / sc[S_RHO_OLD]) * (sc[S_ALPHA] / sc[S_OMEGA]);
     sc[S_ITS] += 1.0;
     if (!isfinite(nr)) sc[S_DONE] = 2.0;
     else if (stop_test(nr, sc)) sc[S_DONE] = 1.0;
@@ -453,7 +459,7 @@ __global__ void k_gm_residual(int64_t N, Offsets of, double* sc, const T* __rest
     }
     const T wi = (T)rhs[i] - s;
     w[i] = wi;
-    acc[0] = (double)wi * (double)wi;
+    acc[0] = (double)(wi * wi);
   }
   double tot[1];
   if (!last_block_sums<1>(acc, part, gridDim.x, counter, tot)) return;
@@ -511,44 +517,64 @@ __global__ void k_gm_spmv(int64_t N, Offsets of, const double* __restrict__ sc, 
 // sc + outslot (passes 1, 2) or completes Hessenberg column k (pass 3): H[0..k][k] =
 // h1 + h2, H[k+1][k] = ||w||, earlier Givens rotations, a new rotation, the residual
 // estimate |g[k+1]|, the end-of-cycle test and invh = 1 / ||w||.
-template <class T>
-__global__ void k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int outslot, T* __restrict__ w,
-                          const T* __restrict__ V, size_t vstride, double* __restrict__ part, int64_t pstride,
-                          unsigned int* counter) {
+// A thread owns elements and holds all k + 1 running dots in registers (QMAX is the
+// compile-time bound on k + 1, the loops over q are unrolled and predicated), so each
+// element's k + 1 basis values are independent loads in flight together.
+template <class T, int QMAX>
+__global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int outslot,
+                                                 T* __restrict__ w, const T* __restrict__ V, size_t vstride,
+                                                 double* __restrict__ part, int64_t pstride, unsigned int* counter) {
   if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
   const bool want_norm = outslot < 0;
-  __shared__ double hs[kMaxRestart + 1];
-  for (int q = threadIdx.x; q <= k; q += blockDim.x) hs[q] = hslot >= 0 ? sc[hslot + q] : 0.0;
+  __shared__ T hs[QMAX];
+  for (int q = threadIdx.x; q < QMAX; q += blockDim.x) hs[q] = (hslot >= 0 && q <= k) ? (T)sc[hslot + q] : (T)0;
   __syncthreads();
-  double acc[kMaxRestart + 1];
-  for (int q = 0; q <= k; ++q) acc[q] = 0.0;
-  double nrm = 0.0;
+  // running sums in the vector type (a thread sees a handful of elements); widened to
+  // double for the sums across warps and blocks
+  T acc[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) acc[q] = (T)0;
+  T nrm = (T)0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    T v[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) v[q] = q <= k ? V[q * vstride + i] : (T)0;
     T wi = w[i];
     if (hslot >= 0) {
-      for (int q = 0; q <= k; ++q) wi -= (T)hs[q] * V[q * vstride + i];
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) wi -= hs[q] * v[q];
       w[i] = wi;
     }
     if (want_norm) {
-      nrm += (double)wi * (double)wi;
+      nrm = fma(wi, wi, nrm);
     } else {
-      for (int q = 0; q <= k; ++q) acc[q] += (double)wi * (double)V[q * vstride + i];
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q)
+        if (q <= k) acc[q] = fma(wi, v[q], acc[q]);
     }
   }
   const int nq = want_norm ? 1 : k + 1;
-  __shared__ double red[kBlock / 32];
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int q = 0; q < nq; ++q) {
-    double t = warp_sum(want_norm ? nrm : acc[q]);
-    if (lane == 0) red[wp] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) s += red[u];
-      part[q * pstride + blockIdx.x] = s;
+  if (want_norm) {
+    const double t = block_allsum((double)nrm);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  } else {
+    __shared__ double red[kBlock / 32][QMAX];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      if (q > k) break;
+      const T t = warp_sum(acc[q]);
+      if (lane == 0) red[wp][q] = (double)t;
     }
     __syncthreads();
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      double s = 0.0;
+      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) s += red[u][q];
+      part[q * pstride + blockIdx.x] = s;
+    }
   }
+  __threadfence();   // every thread that wrote a partial makes it visible before the count
+  __syncthreads();
   __shared__ bool am_last;
   if (threadIdx.x == 0) {
     __threadfence();
@@ -557,17 +583,25 @@ __global__ void k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int ou
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  double last = 0.0;
-  for (int q = 0; q < nq; ++q) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + q * pstride + b);
-    last = block_allsum(s);
-    if (!want_norm && threadIdx.x == 0) sc[outslot + q] = last;
+  // totals of the nq sums: warp q' takes q = q', q' + 8, ... (block order, fixed)
+  __shared__ double tot[QMAX];
+  {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int q = wp; q < nq; q += nwarp) {
+      double s = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + q * pstride + b);
+      s = warp_sum(s);
+      if (lane == 0) tot[q] = s;
+    }
   }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   *counter = 0u;
-  if (!want_norm) return;
-  const double hk1 = sqrt(last);
+  if (!want_norm) {
+    for (int q = 0; q < nq; ++q) sc[outslot + q] = tot[q];
+    return;
+  }
+  const double hk1 = sqrt(tot[0]);
   double* H = sc + S_HCOL;   // H[row * kMaxRestart + col]
   for (int q = 0; q <= k; ++q) H[q * kMaxRestart + k] = sc[S_H1 + q] + sc[S_H2 + q];
   H[(k + 1) * kMaxRestart + k] = hk1;
@@ -595,6 +629,19 @@ __global__ void k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int ou
   if (stop_test(fabs(g[k + 1]), sc) || sc[S_ITS] >= sc[S_MAXIT] || k + 1 == m || hk1 == 0.0) sc[S_CYCLE_DONE] = 1.0;
 }
 
+// Launch a Gram-Schmidt pass with the smallest register footprint that holds k + 1 dots.
+template <class T>
+void orth_launch(afc_problem_s* p, int G, int64_t N, double* sc, int k, int m, int hslot, int outslot, T* w,
+                 const T* V, size_t vs, double* part, int64_t pst, unsigned int* cnt) {
+  cudaStream_t s = p->stream;
+  if (k + 1 <= 8)
+    AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, 8><<<G, kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt));
+  else if (k + 1 <= 16)
+    AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, 16><<<G, kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt));
+  else
+    AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, 32><<<G, kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt));
+}
+
 // back substitution H y = g for the k_used leading columns, then x += D^{-1} sum_q y_q V_q
 // (every block solves the small triangular system itself)
 template <class T>
@@ -606,6 +653,7 @@ __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restr
   const int ku = (int)sc[S_K_USED];
   if (ku == 0) return;
   __shared__ double ys[kMaxRestart];
+  __shared__ T yt[kMaxRestart];
   if (threadIdx.x == 0) {
     const double* H = sc + S_HCOL;
     for (int q = ku - 1; q >= 0; --q) {
@@ -613,11 +661,12 @@ __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restr
       for (int c = q + 1; c < ku; ++c) s -= H[q * kMaxRestart + c] * ys[c];
       ys[q] = s / H[q * kMaxRestart + q];
     }
+    for (int q = 0; q < ku; ++q) yt[q] = (T)ys[q];
   }
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     T s = 0;
-    for (int q = 0; q < ku; ++q) s += (T)ys[q] * V[q * vstride + i];
+    for (int q = 0; q < ku; ++q) s = fma(yt[q], V[q * vstride + i], s);
     x[i] = x[i] + dinv[i] * s;
   }
 }
@@ -741,7 +790,7 @@ template <class T>
 int gmres_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
                int* its, double* res) {
   const int m = o->gmres_restart;
-  if (m < 1 || m > kMaxRestart) { set_error("gmres_restart must be in 1..64"); return AFC_E_INVALID; }
+  if (m < 1 || m > kMaxRestart) { set_error("gmres_restart must be in 1..32"); return AFC_E_INVALID; }
   // vectors: x, w, z, V_0..V_m
   int st = ensure_work(p, 3 + m + 1, sizeof(T) == 4);
   if (st) return st;
@@ -773,9 +822,9 @@ int gmres_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, c
         constexpr int KT = decltype(kc)::value;
         AFC_LAUNCH(p, "k_gm_spmv", k_gm_spmv<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv));
       });
-      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, -1, S_H1, wv, V, vs, part, G, cnt));
-      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H1, S_H2, wv, V, vs, part, G, cnt));
-      AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt));
+      orth_launch<T>(p, G, N, sc, k, m, -1, S_H1, wv, V, vs, part, G, cnt);
+      orth_launch<T>(p, G, N, sc, k, m, S_H1, S_H2, wv, V, vs, part, G, cnt);
+      orth_launch<T>(p, G, N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt);
       AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z));
     }
     AFC_LAUNCH(p, "k_gm_update", k_gm_update<T><<<G, kBlock, 0, s>>>(N, sc, x, V, vs, dinv, GraphCond{}));
@@ -853,7 +902,7 @@ template <class T>
 int gmres_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
                 cudaStream_t cs, cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier) {
   const int m = o->gmres_restart;
-  if (m < 1 || m > kMaxRestart) { set_error("gmres_restart must be in 1..64"); return AFC_E_INVALID; }
+  if (m < 1 || m > kMaxRestart) { set_error("gmres_restart must be in 1..32"); return AFC_E_INVALID; }
   int st = ensure_work(p, 3 + m + 1, sizeof(T) == 4);
   if (st) return st;
   KrylovWork& w = *p->kw;
@@ -890,12 +939,9 @@ int gmres_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, 
            AFC_LAUNCH(p, "k_gm_normalize", k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V, dinv, z));
            for (int k = 0; k < m; ++k) {
              AFC_LAUNCH(p, "k_gm_spmv", k_gm_spmv<KT, T><<<gr, kBlock, 0, s>>>(N, p->offs, sc, B, z, wv));
-             AFC_LAUNCH(p, "k_gm_orth",
-                        k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, -1, S_H1, wv, V, vs, part, G, cnt));
-             AFC_LAUNCH(p, "k_gm_orth",
-                        k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H1, S_H2, wv, V, vs, part, G, cnt));
-             AFC_LAUNCH(p, "k_gm_orth",
-                        k_gm_orth<T><<<G, kBlock, 0, s>>>(N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt));
+             orth_launch<T>(p, G, N, sc, k, m, -1, S_H1, wv, V, vs, part, G, cnt);
+             orth_launch<T>(p, G, N, sc, k, m, S_H1, S_H2, wv, V, vs, part, G, cnt);
+             orth_launch<T>(p, G, N, sc, k, m, S_H2, -1, wv, V, vs, part, G, cnt);
              AFC_LAUNCH(p, "k_gm_normalize",
                         k_gm_normalize<T><<<G, kBlock, 0, s>>>(N, sc, wv, V + (k + 1) * vs, dinv, z));
            }
