@@ -91,8 +91,10 @@ typedef struct {
   int32_t ksp_maxit;      /* max inner iterations (per solve)                             */
   double ksp_atol;        /* inner stop: ||r||_2 < max(ksp_atol, ksp_rtol * ||r_0||_2)    */
   double ksp_rtol;
-  int32_t gmres_restart;  /* GMRES(m) restart length, 1..64                               */
-  int32_t precision;      /* afc_precision: AFC_MIXED runs the inner solve in FP32        */
+  int32_t gmres_restart;  /* GMRES(m) restart length, 1..32                               */
+  int32_t precision;      /* afc_precision: AFC_MIXED runs the inner solve (CN, stationary)*/
+                          /* or the raw fluxes r_ij (SSP) in FP32; limiter sums, alpha    */
+                          /* and the lumped-mass update stay FP64                         */
   int32_t prelimit;       /* CN: apply Eq. prelimiting (L = 2)                            */
   int32_t graph;          /* 1: run the whole step / solve as one CUDA graph with the     */
                           /* loop control on the device (default); 0: host-driven loop    */
@@ -228,6 +230,64 @@ int afc_apply(afc_problem p, int which, const double* x, double* y);
  * Jacobi-preconditioned BiCGStab or GMRES per the options. */
 int afc_linear_solve(afc_problem p, int system, double dt, const afc_opts* o, const double* rhs,
                      double* x, int* its, double* res);
+
+/* ---- batches of independent problems ------------------------------------------
+ *
+ * A batch runs the explicit FE-SSP step (as afc_step with AFC_SSP2 / AFC_SSP3)
+ * of many independent problems together: every pass of a stage (rate, edges,
+ * factors, correct; see afc_step) covers the rows of all instances in one
+ * launch, so small instances do not leave the GPU idle, and each time step is
+ * one CUDA graph.  Each instance keeps its own arrays and its own stored
+ * solution (afc_set_solution / afc_get_solution still apply), and gives the same
+ * result bit for bit as afc_step on it alone with the same options. */
+typedef struct afc_batch_s* afc_batch;
+
+/* Launch shapes of a batched step. */
+typedef enum {
+  AFC_BATCH_AUTO = 0,       /* the tuned shape for this batch's size class, else PER_STAGE  */
+  AFC_BATCH_PER_PASS = 1,   /* one launch per pass (4 per stage), each over all instances    */
+  AFC_BATCH_PER_STAGE = 2,  /* one persistent cooperative launch per stage; the passes are   */
+                            /* separated by grid-wide barriers with a bounded wait          */
+  AFC_BATCH_PER_STEP = 3    /* one persistent cooperative launch per time step              */
+} afc_batch_mode;
+
+typedef struct {
+  int32_t mode;           /* afc_batch_mode                                               */
+  int32_t block;          /* threads per block = rows per tile: 128, 256 or 512           */
+  int32_t blocks_per_sm;  /* persistent modes: resident blocks per SM, 0 = most that fit  */
+  double ms_per_step;     /* afc_batch_tune: measured device time of one step (output)    */
+} afc_batch_tuning;
+
+/* Batch of `count` assembled problems on one device (at most 65536).  The batch
+ * keeps the handles (not copies): the problems must outlive it and must not be
+ * used by other calls while a batch call runs.  Work is enqueued on the stream
+ * of list[0]. */
+int afc_batch_create(const afc_problem* list, int count, afc_batch* out);
+int afc_batch_destroy(afc_batch b);
+
+/* `nsteps` explicit SSP steps of every instance.  opts->scheme is AFC_SSP2 or
+ * AFC_SSP3, opts->limiter NONE / GALERKIN / ZALESAK, opts->precision FP64 or
+ * MIXED (see afc_opts); opts->graph is ignored (the step is always a graph).
+ * dt: host array of `count` time steps, or NULL to use opts->dt for all.
+ * stats: host array of `count` results (umin, umax, stages) or NULL.
+ * Returns AFC_E_TIMEOUT if a grid barrier of a persistent launch gave up waiting
+ * (the instances' solutions are then undefined).  Synchronises the stream. */
+int afc_batch_step(afc_batch b, const afc_opts* o, const double* dt, int nsteps, afc_stats* stats);
+
+/* Fix the launch shape (mode AFC_BATCH_AUTO returns to the tuned / default one). */
+int afc_batch_set_tuning(afc_batch b, const afc_batch_tuning* t);
+int afc_batch_get_tuning(afc_batch b, afc_batch_tuning* t);
+
+/* Time every launch shape (modes x block sizes x residency) on this batch with
+ * these options, keep the fastest for the batch and for its size class (element
+ * types present, log2 of the total and of the mean node count, precision,
+ * limiter, scheme) for later batches of the process, and return it in *best.
+ * The instances' solutions are saved before and restored after the trials. */
+int afc_batch_tune(afc_batch b, const afc_opts* o, const double* dt, afc_batch_tuning* best);
+
+/* Total nodes of the batch's instances and the number of kernel launches its
+ * calls have issued (either pointer may be NULL). */
+int afc_batch_info(afc_batch b, int64_t* total_nodes, int64_t* launches);
 
 /* ---- diagnostics -------------------------------------------------------------- */
 

@@ -31,6 +31,7 @@ AFC_LIM_NONE, AFC_LIM_GALERKIN, AFC_LIM_ZALESAK, AFC_LIM_MC = 0, 1, 2, 3
 AFC_KSP_BICGSTAB, AFC_KSP_GMRES = 0, 1
 AFC_FP64, AFC_MIXED = 0, 1
 AFC_MAT_MC, AFC_MAT_A, AFC_MAT_D, AFC_MAT_LOW, AFC_MAT_K, AFC_MAT_S = 0, 1, 2, 3, 4, 5
+AFC_BATCH_AUTO, AFC_BATCH_PER_PASS, AFC_BATCH_PER_STAGE, AFC_BATCH_PER_STEP = 0, 1, 2, 3
 
 ELEM = {"p1": AFC_P1, "q1": AFC_Q1}
 
@@ -52,6 +53,11 @@ class afc_opts(C.Structure):
 class afc_stats(C.Structure):
     _fields_ = [("outer_its", C.c_int32), ("inner_its", C.c_int32), ("stages", C.c_int32), ("status", C.c_int32),
                 ("res0", C.c_double), ("res_final", C.c_double), ("umin", C.c_double), ("umax", C.c_double)]
+
+
+class afc_batch_tuning(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("ms_per_step", C.c_double)]
 
 
 _P = C.c_void_p
@@ -85,6 +91,13 @@ _SIGS = {
     "afc_profile": (C.c_int, [_P, C.c_int]),
     "afc_profile_read": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int64), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int64)]),
+    "afc_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P)]),
+    "afc_batch_destroy": (C.c_int, [_P]),
+    "afc_batch_step": (C.c_int, [_P, C.POINTER(afc_opts), _D, C.c_int, C.POINTER(afc_stats)]),
+    "afc_batch_set_tuning": (C.c_int, [_P, C.POINTER(afc_batch_tuning)]),
+    "afc_batch_get_tuning": (C.c_int, [_P, C.POINTER(afc_batch_tuning)]),
+    "afc_batch_tune": (C.c_int, [_P, C.POINTER(afc_opts), _D, C.POINTER(afc_batch_tuning)]),
+    "afc_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "afc_status_str": (C.c_char_p, [C.c_int]),
     "afc_last_error": (C.c_char_p, []),
 }
@@ -335,3 +348,66 @@ class Problem:
                                    C.byref(res))
         _check(st, "afc_linear_solve", allow_not_converged=True)
         return x, its.value, res.value
+
+
+def tuning_dict(t: afc_batch_tuning) -> dict:
+    return {name: getattr(t, name) for name, _ in afc_batch_tuning._fields_}
+
+
+class Batch:
+    """Owner of one afc_batch handle over a list of assembled Problems (kept alive here)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h for p in self.problems])
+        h = C.c_void_p()
+        _check(_lib.afc_batch_create(arr, len(self.problems), C.byref(h)), "afc_batch_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.afc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, opts: afc_opts, dt=None, nsteps=1) -> list:
+        n = len(self.problems)
+        dta = None if dt is None else _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)), n)
+        stats = (afc_stats * n)()
+        _check(_lib.afc_batch_step(self.h, C.byref(opts), None if dta is None else _dp(dta), int(nsteps), stats),
+               "afc_batch_step")
+        return [stats_dict(s) for s in stats]
+
+    def set_tuning(self, mode, block=256, blocks_per_sm=0):
+        t = afc_batch_tuning(mode, block, blocks_per_sm, 0.0)
+        _check(_lib.afc_batch_set_tuning(self.h, C.byref(t)), "afc_batch_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = afc_batch_tuning()
+        _check(_lib.afc_batch_get_tuning(self.h, C.byref(t)), "afc_batch_get_tuning")
+        return tuning_dict(t)
+
+    def tune(self, opts: afc_opts, dt=None) -> dict:
+        n = len(self.problems)
+        dta = None if dt is None else _f64(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)), n)
+        t = afc_batch_tuning()
+        _check(_lib.afc_batch_tune(self.h, C.byref(opts), None if dta is None else _dp(dta), C.byref(t)),
+               "afc_batch_tune")
+        return tuning_dict(t)
+
+    def info(self) -> tuple[int, int]:
+        """(total nodes, kernel launches issued by the batch's calls)."""
+        tn, nl = C.c_int64(), C.c_int64()
+        _check(_lib.afc_batch_info(self.h, C.byref(tn), C.byref(nl)), "afc_batch_info")
+        return tn.value, nl.value

@@ -150,6 +150,9 @@ struct afc_problem_s {
   afc::DBuf<unsigned int> clip;     // MC: per row, bit ku set if the pair (i, i + o) was clipped
   afc::DBuf<float4> nodef;          // MC: (u, u_max - u, u - u_min) rounded to single
   afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
+  // mixed-precision explicit stage: m_ij, d_ij, r_ij (Kup * N) and u, udot^L (node vectors) in single
+  afc::DBuf<float> m32_up, d32_up, r32, uf, udf;
+  bool ssp32_ready = false;         // m32_up / d32_up match the assembled m_up / d_up
   afc::DBuf<double> scal;           // small device scalars (norms, dt, ...)
   afc::DBuf<double> part;           // reduction partials
   double* host_scal = nullptr;      // pinned host mirror of scal
@@ -172,7 +175,10 @@ int build_cn_system(afc_problem_s* p, double dt);
 // ---- kernels of the hot path (fct.cu, mc.cu) ----
 // SSP forward-Euler stage: out = a * uA + b * FE(uin) (Eq. FE-SSP with Zalesak).
 int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double a, const double* uA, double b,
-             double* out);
+             double* out, bool mixed = false);
+int ensure_ssp_mixed(afc_problem_s* p);   // single-precision copies of m_ij, d_ij for the mixed stage
+struct SspArrays;
+SspArrays ssp_arrays(afc_problem_s* p);
 // CN helpers
 int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
 // a = u - u_old, s = u + u_old after u += omega * delta (delta may be null)

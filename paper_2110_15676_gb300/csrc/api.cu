@@ -424,6 +424,7 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
     return AFC_E_INVALID;
   }
   cudaStream_t s = p->stream;
+  const bool mixed = o->precision == AFC_MIXED;
   const bool graph = o->graph != 0;   // captured on a private stream, launched on the problem's stream
   if (graph && (o->scheme == AFC_SSP2 || o->scheme == AFC_SSP3)) return ssp_step_graph(p, o, stt);
   if (graph && o->scheme == AFC_CN_NONLINEAR) {
@@ -433,15 +434,15 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   }
   AFC_CUDA(cudaMemcpyAsync(p->u0.p, p->u.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (o->scheme == AFC_SSP2) {
-    if ((st = fe_stage(p, p->u0.p, o->dt, lim, 0.0, nullptr, 1.0, p->ustage.p))) return st;
-    if ((st = fe_stage(p, p->ustage.p, o->dt, lim, 0.5, p->u0.p, 0.5, p->u.p))) return st;
+    if ((st = fe_stage(p, p->u0.p, o->dt, lim, 0.0, nullptr, 1.0, p->ustage.p, mixed))) return st;
+    if ((st = fe_stage(p, p->ustage.p, o->dt, lim, 0.5, p->u0.p, 0.5, p->u.p, mixed))) return st;
     if (stt) stt->stages = 2;
     return finish_stats(p, stt, AFC_OK);
   }
   if (o->scheme == AFC_SSP3) {
-    if ((st = fe_stage(p, p->u0.p, o->dt, lim, 0.0, nullptr, 1.0, p->ustage.p))) return st;
-    if ((st = fe_stage(p, p->ustage.p, o->dt, lim, 0.75, p->u0.p, 0.25, p->tmp.p))) return st;
-    if ((st = fe_stage(p, p->tmp.p, o->dt, lim, 1.0 / 3.0, p->u0.p, 2.0 / 3.0, p->u.p))) return st;
+    if ((st = fe_stage(p, p->u0.p, o->dt, lim, 0.0, nullptr, 1.0, p->ustage.p, mixed))) return st;
+    if ((st = fe_stage(p, p->ustage.p, o->dt, lim, 0.75, p->u0.p, 0.25, p->tmp.p, mixed))) return st;
+    if ((st = fe_stage(p, p->tmp.p, o->dt, lim, 1.0 / 3.0, p->u0.p, 2.0 / 3.0, p->u.p, mixed))) return st;
     if (stt) stt->stages = 3;
     return finish_stats(p, stt, AFC_OK);
   }

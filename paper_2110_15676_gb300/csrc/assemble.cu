@@ -303,6 +303,7 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
   p->family = family;
   p->precision = precision;
   p->cn_dt = -1.0;
+  p->ssp32_ready = false;
   p->assembled = true;
   return AFC_OK;
 }

@@ -12,121 +12,42 @@
 // on the integer pipe (kernels_common.cuh).
 #include "afc_internal.h"
 #include "kernels_common.cuh"
+#include "ssp_rows.cuh"
 
 namespace afc {
 
 namespace {
 
-// ---- explicit stage -----------------------------------------------------------
+// ---- explicit stage (per-row arithmetic in ssp_rows.cuh) ------------------------
 
-// y = AA u;  udot^L = (f - y) / m (0 at Dirichlet nodes, whose data is constant);
-// predictor u~ = u + dt (f - y) / m, u~ = u_D at Dirichlet nodes.
-template <int KT>
-__global__ void k_ssp_rate(int64_t N, Offsets of, const double* __restrict__ AA, const double* __restrict__ u,
-                           const double* __restrict__ f, const double* __restrict__ mL,
-                           const uint8_t* __restrict__ dir, const double* __restrict__ udir, double dt,
-                           double* __restrict__ udot, double* __restrict__ ut) {
-  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double y = 0.0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], u[i + of.o[k]], y);
-  if (dir[i]) {
-    udot[i] = 0.0;
-    ut[i] = udir[i];
-  } else {
-    const double fy = f[i] - y;
-    udot[i] = fy / mL[i];
-    ut[i] = u[i] + dt * fy / mL[i];
-  }
+template <int KT, bool MIXED>
+__global__ void k_ssp_rate(Offsets of, SspArrays a, const double* __restrict__ u, double dt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.N) ssp_rate_row<KT, MIXED>(of, a, i, u, dt);
 }
 
-// Eq. defn_r_ij_SSP for every pair i < j: r_ij = m_ij (udot_i - udot_j) + d_ij (u_j - u_i).
-// Pairs outside the pattern have m = d = 0 and get r = 0.
-// One thread per pair slot: block = 32 rows (threadIdx.x) x all upper offsets (threadIdx.y).
-template <int KT>
-__global__ void k_ssp_edges(int64_t N, Offsets of, const double* __restrict__ m_up, const double* __restrict__ d_up,
-                            const double* __restrict__ u, const double* __restrict__ udot,
-                            double* __restrict__ r_up) {
-  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
-  const int ku = threadIdx.y;
-  const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
-  if (i >= N) return;
-  const int64_t q = (int64_t)ku * N + i;
-  const int64_t j = i + of.o[Kup + 1 + ku];
-  r_up[q] = fma(m_up[q], udot[i] - udot[j], d_up[q] * (u[j] - u[i]));
+template <int KT, bool MIXED>
+__global__ void k_ssp_edges(Offsets of, SspArrays a, const double* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.N) ssp_edges_row<KT, MIXED>(of, a, i, u);
 }
 
-// Zalesak steps 1-3: P+/- from the stored fluxes, Q+/- from the predictor over N_i, R+/-.
-template <int KT>
-__global__ void k_ssp_factors(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
-                              const double* __restrict__ r_up, const double* __restrict__ ut,
-                              const double* __restrict__ mL, const uint8_t* __restrict__ dir, double dt,
-                              double* __restrict__ Rp, double* __restrict__ Rm) {
-  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
-  const unsigned long long mk = mask[i];
-  const double uti = ut[i];
-  double Pp = 0.0, Pm = 0.0;
-  long long kmax = dkey(uti), kmin = kmax;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (k == Kup || !((mk >> k) & 1ull)) continue;
-    const double r = pair_flux(of, Kup, k, i, N, r_up);
-    if (gt0(r)) Pp += r;
-    else if (!is0(r)) Pm += r;
-    const long long kj = dkey(ut[i + of.o[k]]);
-    kmax = kj > kmax ? kj : kmax;
-    kmin = kj < kmin ? kj : kmin;
-  }
-  // >= 0 and <= 0: the max / min include i itself
-  const double Qp = from_key(kmax) - uti, Qm = from_key(kmin) - uti;
-  const double m = mL[i];
-  Rp[i] = zalesak_factor(m * Qp, dt * Pp);
-  Rm[i] = zalesak_factor(m * Qm, dt * Pm);
+template <int KT, bool MIXED>
+__global__ void k_ssp_factors(Offsets of, SspArrays a, double dt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.N) ssp_factors_row<KT, MIXED>(of, a, i, dt);
 }
 
-// Zalesak step 4 and the update: F*_i = sum_j alpha_ij r_ij,
-// u_new = u~ + dt F* / m (= u + dt (f + F* - AA u) / m, Eq. FE-SSP), Dirichlet: u_D;
-// out = a * uA + b * u_new (the SSP combination of the stage).
-template <int KT>
-__global__ void k_ssp_correct(int64_t N, Offsets of, int limiter, const unsigned long long* __restrict__ mask,
-                              const double* __restrict__ r_up, const double* __restrict__ ut,
-                              const double* __restrict__ Rp, const double* __restrict__ Rm,
-                              const double* __restrict__ mL, const uint8_t* __restrict__ dir,
-                              const double* __restrict__ udir, double dt, double a, const double* __restrict__ uA,
-                              double b, double* __restrict__ out, double* __restrict__ Fout) {
-  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double unew;
-  double F = 0.0;
-  if (dir[i]) {
-    unew = udir[i];
-  } else {
-    if (limiter != AFC_LIM_NONE) {
-      const unsigned long long mk = mask[i];
-      const double rpi = Rp[i], rmi = Rm[i];
-    #pragma unroll
-  for (int k = 0; k < K; ++k) {
-        if (k == Kup || !((mk >> k) & 1ull)) continue;
-        const double r = pair_flux(of, Kup, k, i, N, r_up);
-        if (limiter == AFC_LIM_ZALESAK) {
-          const int64_t j = i + of.o[k];
-          const double alpha = gt0(r) ? imin_nn(rpi, Rm[j]) : imin_nn(rmi, Rp[j]);
-          F = fma(alpha, r, F);
-        } else {
-          F += r;
-        }
-      }
-    }
-    unew = ut[i] + dt * F / mL[i];
-  }
-  if (Fout) Fout[i] = F;
-  out[i] = a != 0.0 ? a * uA[i] + b * unew : b * unew;
+template <int KT, bool MIXED>
+__global__ void k_ssp_correct(Offsets of, SspArrays a, int limiter, double dt, double ca,
+                              const double* __restrict__ uA, double cb, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.N) ssp_correct_row<KT, MIXED>(of, a, i, limiter, dt, ca, uA, cb, out);
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __double2float_rn(x[i]);
 }
 
 // ---- Crank-Nicolson -------------------------------------------------------------
@@ -277,25 +198,69 @@ __global__ void k_cn_residual(int64_t N, Offsets of, int limiter, const unsigned
 
 }  // namespace
 
+SspArrays ssp_arrays(afc_problem_s* p) {
+  SspArrays a;
+  a.N = p->N;
+  a.AA = p->AA.p;
+  a.m_up = p->m_up.p;
+  a.d_up = p->d_up.p;
+  a.m32 = p->m32_up.p;
+  a.d32 = p->d32_up.p;
+  a.mL = p->mL.p;
+  a.f = p->f.p;
+  a.dir = p->dir.p;
+  a.udir = p->udir.p;
+  a.mask = p->mask.p;
+  a.udot = p->udot.p;
+  a.ut = p->ut.p;
+  a.uf = p->uf.p;
+  a.udf = p->udf.p;
+  a.r_up = p->r_up.p;
+  a.r32 = p->r32.p;
+  a.Rp = p->Rp.p;
+  a.Rm = p->Rm.p;
+  a.Fs = p->Fs.p;
+  return a;
+}
+
+int ensure_ssp_mixed(afc_problem_s* p) {
+  if (p->ssp32_ready) return AFC_OK;
+  const int64_t N = p->N, Kup = p->Kup;
+  int st;
+  if ((st = p->m32_up.alloc(Kup * N)) || (st = p->d32_up.alloc(Kup * N)) || (st = p->r32.alloc(Kup * N)) ||
+      (st = p->uf.alloc(N, p->pad)) || (st = p->udf.alloc(N, p->pad)))
+    return st;
+  AFC_LAUNCH(p, "k_to_float", k_to_float<<<grid_for(Kup * N), kBlock, 0, p->stream>>>(Kup * N, p->m_up.p, p->m32_up.p));
+  AFC_LAUNCH(p, "k_to_float", k_to_float<<<grid_for(Kup * N), kBlock, 0, p->stream>>>(Kup * N, p->d_up.p, p->d32_up.p));
+  AFC_CUDA(cudaGetLastError());
+  p->ssp32_ready = true;
+  return AFC_OK;
+}
+
 int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double a, const double* uA, double b,
-             double* out) {
+             double* out, bool mixed) {
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
-  with_K(p->K, [&](auto kc) {
+  if (mixed) {
+    int st = ensure_ssp_mixed(p);
+    if (st) return st;
+  }
+  const SspArrays arr = ssp_arrays(p);
+  auto run = [&](auto kc, auto mc) {
     constexpr int KT = decltype(kc)::value;
-    AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->AA.p, uin, p->f.p, p->mL.p,
-                                                                     p->dir.p, p->udir.p, dt, p->udot.p, p->ut.p));
+    constexpr bool MX = decltype(mc)::value;
+    AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT, MX><<<g, kBlock, 0, s>>>(p->offs, arr, uin, dt));
     if (limiter != AFC_LIM_NONE)
-      AFC_LAUNCH(p, "k_ssp_edges", k_ssp_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(N, p->offs, p->m_up.p, p->d_up.p, uin,
-                                                                         p->udot.p, p->r_up.p));
+      AFC_LAUNCH(p, "k_ssp_edges", k_ssp_edges<KT, MX><<<g, kBlock, 0, s>>>(p->offs, arr, uin));
     if (limiter == AFC_LIM_ZALESAK)
-      AFC_LAUNCH(p, "k_ssp_factors", k_ssp_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->ut.p,
-                                                                             p->mL.p, p->dir.p, dt, p->Rp.p, p->Rm.p));
+      AFC_LAUNCH(p, "k_ssp_factors", k_ssp_factors<KT, MX><<<g, kBlock, 0, s>>>(p->offs, arr, dt));
     AFC_LAUNCH(p, "k_ssp_correct",
-               k_ssp_correct<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->r_up.p, p->ut.p, p->Rp.p,
-                                                      p->Rm.p, p->mL.p, p->dir.p, p->udir.p, dt, a, uA, b, out,
-                                                      p->Fs.p));
+               k_ssp_correct<KT, MX><<<g, kBlock, 0, s>>>(p->offs, arr, limiter, dt, a, uA, b, out));
+  };
+  with_K(p->K, [&](auto kc) {
+    if (mixed) run(kc, std::true_type{});
+    else run(kc, std::false_type{});
   });
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;

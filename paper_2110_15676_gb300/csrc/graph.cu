@@ -357,6 +357,11 @@ int stationary_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
 }
 
 int ssp_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
+  const bool mixed = o->precision == AFC_MIXED;
+  if (mixed) {
+    int s0 = ensure_ssp_mixed(p);   // allocation and conversion stay outside the capture
+    if (s0) return s0;
+  }
   const auto key = make_key(p, o, 3);
   if (!p->g_step || p->g_step->key != key) {
     drop(p->g_step);
@@ -374,12 +379,12 @@ int ssp_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
       AFC_LAUNCH(p, "k_copy", k_copy<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->u.p, p->u0.p));
       int s;
       if (o->scheme == AFC_SSP2) {
-        if ((s = fe_stage(p, p->u0.p, dt, lim, 0.0, nullptr, 1.0, p->ustage.p))) return s;
-        if ((s = fe_stage(p, p->ustage.p, dt, lim, 0.5, p->u0.p, 0.5, p->u.p))) return s;
+        if ((s = fe_stage(p, p->u0.p, dt, lim, 0.0, nullptr, 1.0, p->ustage.p, mixed))) return s;
+        if ((s = fe_stage(p, p->ustage.p, dt, lim, 0.5, p->u0.p, 0.5, p->u.p, mixed))) return s;
       } else {
-        if ((s = fe_stage(p, p->u0.p, dt, lim, 0.0, nullptr, 1.0, p->ustage.p))) return s;
-        if ((s = fe_stage(p, p->ustage.p, dt, lim, 0.75, p->u0.p, 0.25, p->tmp.p))) return s;
-        if ((s = fe_stage(p, p->tmp.p, dt, lim, 1.0 / 3.0, p->u0.p, 2.0 / 3.0, p->u.p))) return s;
+        if ((s = fe_stage(p, p->u0.p, dt, lim, 0.0, nullptr, 1.0, p->ustage.p, mixed))) return s;
+        if ((s = fe_stage(p, p->ustage.p, dt, lim, 0.75, p->u0.p, 0.25, p->tmp.p, mixed))) return s;
+        if ((s = fe_stage(p, p->tmp.p, dt, lim, 1.0 / 3.0, p->u0.p, 2.0 / 3.0, p->u.p, mixed))) return s;
       }
       return enqueue_stats(p);
     }, fr);
