@@ -242,6 +242,173 @@ def mc_sweep(afc, W, torch, flush, stream, reps):
     return out
 
 
+def batched(afc, W, torch, stream, steps=50, count=256, seed=4, shape=None, solo=True):
+    """256 independent transient Q1 problems (nodes per side uniform in [17, 49], eps
+    log-uniform in [1e-8, 1e-4], random constant unit b, random hump centre), 50
+    SSP3 Zalesak steps each at CFL 0.5: batched mixed precision, batched FP64 and the
+    plain one-at-a-time FP64 path (afc_step per instance and step)."""
+    rng = np.random.default_rng(seed)
+    wls = [W.random_transient(rng, "q1", (17, 49)) for _ in range(count)]
+    gs = []
+    N = nnz = E = 0
+    for wl in wls:
+        g = afc.Problem.structured(wl.elem, wl.n)
+        g.set_coefficients(wl.eps, wl.b, wl.c, wl.f)
+        g.set_dirichlet(wl.dir_mask, wl.u_dir)
+        g.assemble(afc.AFC_FAMILY_FCT, afc.AFC_FP64)
+        g.set_solution(wl.u0)
+        inf = g.info()
+        N += inf["n_nodes"]
+        nnz += inf["nnz"]
+        E += inf["n_edges"]
+        gs.append(g)
+    dts = [g.cfl_timestep(0.5) for g in gs]
+
+    def reset():
+        for g, wl in zip(gs, wls):
+            g.set_solution(wl.u0)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    b = afc.Batch(gs)
+    res = {}
+    sols = {}
+    for name, prec in (("mixed", afc.AFC_MIXED), ("fp64", afc.AFC_FP64)):
+        opts = afc.default_opts(scheme=afc.AFC_SSP3, precision=prec)
+        if shape is None:
+            tuning = b.tune(opts, dt=dts)
+        else:
+            b.set_tuning(*shape)
+            tuning = b.get_tuning()
+        reset()
+        b.step(opts, dt=dts, nsteps=2)   # warm
+        reset()
+        _, l0 = b.info()
+        ms = timed(lambda: b.step(opts, dt=dts, nsteps=steps))
+        _, l1 = b.info()
+        sols[name] = [g.get_solution() for g in gs]
+        umin = min(float(u.min()) for u in sols[name])
+        umax = max(float(u.max()) for u in sols[name])
+        # algorithmic FP64 work per stage: SpMV 2 nnz, raw fluxes 5 per pair (FP64 only),
+        # P+/- 1 per directed pair, alpha r 2 per directed pair, 16 per node
+        flops = 3 * steps * (2.0 * nnz + (5.0 * E if prec == afc.AFC_FP64 else 0.0) + 6.0 * E + 16.0 * N)
+        res[name] = {"ms": ms, "solves_per_s": count / (ms / 1e3), "dof_stages_per_s": N * 3 * steps / (ms / 1e3),
+                     "tuning": tuning, "gpu_launches": l1 - l0 - 1, "umin": umin, "umax": umax,
+                     "alu": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}}
+    b.close()
+    # the plain path: one problem at a time, afc_step (FP64, one CUDA graph per step)
+    reset()
+    ms_solo = 0.0
+    for q, g in enumerate(gs if solo else []):
+        o = afc.default_opts(scheme=afc.AFC_SSP3, dt=dts[q])
+        g.step(o)   # graph build
+        g.set_solution(wls[q].u0)
+
+        def run(g=g, o=o):
+            for _ in range(steps):
+                g.step(o)
+        ms_solo += timed(run)
+    solo_u = [g.get_solution() for g in gs]
+    same = all(np.array_equal(a, c) for a, c in zip(solo_u, sols["fp64"])) if solo else None
+    err = max(float(np.abs(m - f).max()) for m, f in zip(sols["mixed"], sols["fp64"]))
+    scale = max(float(np.abs(f).max()) for f in sols["fp64"])
+    for g in gs:
+        g.close()
+    return {"workload": f"{count} independent transient Q1 problems, nodes per side uniform in [17, 49] "
+                        f"(numpy default_rng({seed})), eps log-uniform [1e-8, 1e-4], random unit constant b, hump "
+                        f"radius 0.15 at a random centre; SSP3 Zalesak FCT, CFL 0.5, {steps} steps",
+            "instances": count, "total_dofs": N, "nnz": nnz, "edges": E, "steps": steps,
+            "batched_mixed": res["mixed"], "batched_fp64": res["fp64"],
+            "one_at_a_time_fp64": {"ms": ms_solo, "solves_per_s": count / (ms_solo / 1e3),
+                                   "dof_stages_per_s": N * 3 * steps / (ms_solo / 1e3)} if solo else None,
+            "speedup_mixed_vs_one_at_a_time_fp64": ms_solo / res["mixed"]["ms"] if solo else None,
+            "mixed_max_abs_diff_vs_fp64": err, "mixed_rel_diff_vs_fp64": err / scale,
+            "batched_fp64_bitwise_equal_to_one_at_a_time": same}
+
+
+def serving(afc, W, rates=(20.0, 100.0, 500.0), count=48, seed=5, stat_maxit=50):
+    """Poisson streams of stationary and transient CDR requests (P1 or Q1, nodes per
+    side uniform in [17, 97], eps log-uniform [1e-8, 1e-4], c uniform [0, 1]):
+    the batched server with mixed precision against the serial server with FP64
+    (one request at a time), latency p50 / p99 and solves/s per arrival rate."""
+    mix = W.serving_mix(np.random.default_rng(seed), count)
+
+    def opts(kind, prec):
+        if kind == "transient":
+            return afc.default_opts(scheme=afc.AFC_SSP3, precision=prec)
+        return afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
+                                ksp_rtol=1e-6, fp_tol=1e-8, fp_maxit=stat_maxit, precision=prec)
+
+    def reqs(prec):
+        out = []
+        for kind, wl in mix:
+            k = afc.AFC_REQ_TRANSIENT if kind == "transient" else afc.AFC_REQ_STATIONARY
+            out.append(afc.Request(k, wl.elem, wl.n, wl.eps, wl.c, wl.b, wl.u0, wl.dir_mask, wl.u_dir, f=wl.f,
+                                   opts=opts(kind, prec), steps=50, cfl=0.5))
+        return out
+
+    arms = {"batched_mixed": (afc.AFC_SERVE_BATCHED, reqs(afc.AFC_MIXED)),
+            "serial_fp64": (afc.AFC_SERVE_SERIAL, reqs(afc.AFC_FP64))}
+    rows = []
+    sols = {}
+    for rate in rates:
+        arr = np.cumsum(np.random.default_rng(int(seed * 1000 + rate)).exponential(1.0 / rate, size=count))
+        row = {"rate_per_s": rate}
+        for name, (mode, rq) in arms.items():
+            with afc.Server(mode=mode, stationary_workers=4, max_chunk=10) as srv:
+                t0 = time.perf_counter()
+                ids = []
+                for t_arr, r in zip(arr, rq):
+                    dt = t0 + t_arr - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    ids.append(srv.submit(r))
+                lat, done, first, states, failed = [], [], None, [], []
+                for q, rid in enumerate(ids):
+                    res, u = srv.wait(rid, timeout=-1.0, want_u=(rate == rates[-1]))
+                    states.append(res["state"])
+                    if res["state"] != afc.AFC_REQ_DONE:
+                        kind, wl = mix[q]
+                        failed.append({"request": q, "kind": kind, "name": wl.name, "state": res["state"],
+                                       "status": res["status"], "message": res["message"]})
+                    lat.append(res["t_done"] - res["t_submit"])
+                    done.append(res["t_done"])
+                    first = res["t_submit"] if first is None else min(first, res["t_submit"])
+                    if u is not None:
+                        sols.setdefault(name, []).append(u)
+                    srv.release(rid)
+                info = srv.info()
+            lat = np.asarray(lat) * 1e3
+            span = max(done) - first
+            row[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "solves_per_s": count / span, "makespan_s": span,
+                         "done": int(sum(s == afc.AFC_REQ_DONE for s in states)),
+                         "max_batch": info["max_batch"], "chunks": info["chunks"], "not_done": failed,
+                         "p50_ms_by_kind": {k: float(np.percentile([l for l, (kk, _) in zip(lat, mix) if kk == k], 50))
+                                            for k in ("stationary", "transient")}}
+        row["speedup_solves_per_s"] = row["batched_mixed"]["solves_per_s"] / row["serial_fp64"]["solves_per_s"]
+        rows.append(row)
+    diff = max((float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+                for a, b in zip(sols["batched_mixed"], sols["serial_fp64"]) if np.abs(a).max() > 0), default=None)
+    n_st = sum(k == "stationary" for k, _ in mix)
+    return {"workload": f"{count} requests (numpy default_rng({seed})): {n_st} stationary MC (inflow problem, omega 0.5, "
+                        f"tol 1e-8, at most {stat_maxit} fixed-point iterations, Jacobi-GMRES(20) rtol 1e-6), "
+                        f"{count - n_st} transient SSP3 Zalesak (50 steps, CFL 0.5); P1/Q1, n in [17, 97], eps "
+                        f"log-uniform [1e-8, 1e-4], c in [0, 1]; Poisson arrivals",
+            "rates": rows, "mixed_max_rel_diff_vs_fp64": diff,
+            "arms": "batched_mixed: continuous batching of transient requests, 4 concurrent stationary solves, "
+                    "FP32 inner solves / fluxes; serial_fp64: one request at a time, FP64"}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -250,6 +417,18 @@ def run_ours(args, ws, rank, local):
     from paper_2110_15676_gb300 import workloads as W
 
     torch.cuda.set_device(local)
+    if args.only_serving:
+        print(json.dumps({"serving": serving(afc, W, count=args.serving_count)}))
+        return
+    if args.only_batched:
+        shape = None
+        if args.batched_mode != "auto":
+            mode = {"pass": afc.AFC_BATCH_PER_PASS, "stage": afc.AFC_BATCH_PER_STAGE,
+                    "step": afc.AFC_BATCH_PER_STEP}[args.batched_mode]
+            shape = (mode, args.batched_block)
+        print(json.dumps({"batched": batched(afc, W, torch, torch.cuda.current_stream(), count=args.batched_count,
+                                             shape=shape, solo=not args.no_solo)}))
+        return
     if args.only_mc_sweep:
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         print(json.dumps({"mc_sweep": mc_sweep(afc, W, torch, flush, torch.cuda.current_stream(),
@@ -344,6 +523,14 @@ def run_ours(args, ws, rank, local):
         del P
         sweep = mc_sweep(afc, W, torch, flush, stream, max(args.steps, 5))
 
+    bat = None
+    if not args.no_batched and args.steps > 0:
+        bat = batched(afc, W, torch, stream)
+
+    srv = None
+    if not args.no_serving and args.steps > 0:
+        srv = serving(afc, W, count=args.serving_count)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_its)
@@ -361,7 +548,7 @@ def run_ours(args, ws, rank, local):
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]},
             "kernel_times": "second pass of the same steps, launches issued one by one with per-launch CUDA "
                             "events (the timed pass runs each step as one CUDA graph)",
-            "mixed": mixed, "mc_sweep": sweep, "cpu_baseline": cpu,
+            "mixed": mixed, "mc_sweep": sweep, "batched": bat, "serving": srv, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -427,6 +614,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mc-sweep", action="store_true")
     ap.add_argument("--only-mc-sweep", action="store_true", help="time only the P1 129^3 MC sweep")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--only-batched", action="store_true", help="time only the 256-instance batched SSP3 run")
+    ap.add_argument("--batched-count", type=int, default=256, help="instances of the batched run (--only-batched)")
+    ap.add_argument("--batched-mode", default="auto", choices=["auto", "pass", "stage", "step"],
+                    help="launch shape of the batched run (--only-batched); auto = tuned")
+    ap.add_argument("--batched-block", type=int, default=128)
+    ap.add_argument("--no-solo", action="store_true", help="skip the one-at-a-time path (--only-batched)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--only-serving", action="store_true", help="time only the request-server streams")
+    ap.add_argument("--serving-count", type=int, default=48)
     ap.add_argument("--cpu-sample-its", type=int, default=6)
     args = ap.parse_args()
     ws, rank, local = _dist()

@@ -289,6 +289,98 @@ int afc_batch_tune(afc_batch b, const afc_opts* o, const double* dt, afc_batch_t
  * calls have issued (either pointer may be NULL). */
 int afc_batch_info(afc_batch b, int64_t* total_nodes, int64_t* launches);
 
+/* ---- a request server ------------------------------------------------------------
+ *
+ * A server solves requests (a transient SSP run or a stationary solve of one CDR
+ * problem on a box grid) submitted from any thread, with the problems' data
+ * resident on the device while they run:
+ *  - AFC_SERVE_BATCHED: an admission thread admits requests in arrival order
+ *    while their estimated device memory fits the budget and the slot count
+ *    allows, and builds their problems; all admitted transient requests advance
+ *    together in batched SSP steps (afc_batch_step), in chunks of at most
+ *    max_chunk steps, and requests admitted meanwhile join at the next chunk;
+ *    stationary requests run concurrently, each on its own stream, on
+ *    `stationary_workers` threads.
+ *  - AFC_SERVE_SERIAL: one request at a time in arrival order (afc_step per
+ *    step, afc_solve_stationary), nothing overlapped: the plain baseline.
+ * A request's result does not depend on the other requests (a batched step
+ * gives an instance the same bits as afc_step). */
+typedef struct afc_server_s* afc_server;
+
+typedef enum { AFC_REQ_TRANSIENT = 0, AFC_REQ_STATIONARY = 1 } afc_request_kind;
+typedef enum { AFC_SERVE_BATCHED = 0, AFC_SERVE_SERIAL = 1 } afc_serve_mode;
+typedef enum {
+  AFC_REQ_PENDING = 0,    /* submitted, not admitted                                     */
+  AFC_REQ_RUNNING = 1,    /* admitted: problem resident on the device                    */
+  AFC_REQ_DONE = 2,       /* finished; status may be AFC_NOT_CONVERGED                    */
+  AFC_REQ_FAILED = 3,     /* a library call failed; status holds its code                 */
+  AFC_REQ_CANCELLED = 4
+} afc_request_state;
+
+typedef struct {
+  int32_t kind;           /* afc_request_kind                                              */
+  int32_t elem;           /* afc_elem                                                      */
+  int32_t n[3];           /* nodes per side of the box grid                                */
+  double lo[3], hi[3];    /* the box                                                       */
+  double eps, c;          /* diffusion, reaction                                           */
+  const double* b;        /* 3N nodal velocity (copied at submission)                      */
+  const double* f;        /* N nodal source, or NULL                                       */
+  const uint8_t* dir_mask;/* N                                                             */
+  const double* u_dir;    /* N Dirichlet values                                            */
+  const double* u0;       /* N initial data (transient) or initial guess (stationary)     */
+  int32_t family;         /* afc_family to assemble                                        */
+  int32_t steps;          /* transient: number of steps                                    */
+  double cfl;             /* transient: dt = cfl * min m_i / AA_ii unless opts.dt > 0      */
+  afc_opts opts;          /* scheme (SSP2 / SSP3), limiter, precision, solver settings     */
+} afc_request;
+
+typedef struct {
+  int32_t state;          /* afc_request_state                                             */
+  int32_t status;         /* afc_status of the solve                                       */
+  afc_stats stats;        /* transient: stages, umin, umax; stationary: as afc_solve_stationary */
+  int64_t n_nodes;
+  double t_submit, t_admit, t_done;   /* seconds on the server's clock                     */
+  char message[160];      /* FAILED: the library's error detail                            */
+} afc_result;
+
+typedef struct {
+  int32_t mode;               /* afc_serve_mode                                            */
+  int32_t max_active;         /* requests admitted at once                                 */
+  int64_t hbm_budget;         /* device bytes admitted requests may hold (estimated)       */
+  int32_t stationary_workers; /* concurrent stationary solves (1..64)                      */
+  int32_t max_chunk;          /* transient steps per batched call                          */
+} afc_serve_config;
+
+typedef struct {
+  int64_t pending, active, bytes_in_use, completed, failed;
+  int64_t chunks;             /* batched calls issued                                      */
+  int64_t batched_steps;      /* steps advanced by those calls                             */
+  int64_t max_batch;          /* most transient requests in one batch                      */
+  double clock;               /* seconds since the server started                          */
+} afc_serve_info;
+
+void afc_serve_default_config(afc_serve_config* c);
+/* Device bytes the server reserves for a request while it runs (host only). */
+int64_t afc_serve_estimate_bytes(const afc_request* r);
+int afc_serve_create(int device, const afc_serve_config* cfg, afc_server* out);
+/* Copies the request's arrays; returns at once with its id.  AFC_E_INVALID if the
+ * request is malformed or alone exceeds the budget. */
+int afc_serve_submit(afc_server s, const afc_request* r, int64_t* id);
+/* Current state of a request; if it is done, u_out (n_nodes host doubles, may be
+ * NULL) receives the solution. */
+int afc_serve_poll(afc_server s, int64_t id, afc_result* res, double* u_out);
+/* As poll, after waiting until the request has finished (timeout_s < 0: no
+ * limit); AFC_E_TIMEOUT if it has not finished in time. */
+int afc_serve_wait(afc_server s, int64_t id, double timeout_s, afc_result* res, double* u_out);
+/* Pending requests are dropped; running transient requests leave at the next
+ * chunk; a running stationary solve finishes first.  The state becomes CANCELLED. */
+int afc_serve_cancel(afc_server s, int64_t id);
+/* Forget a finished request (its result). */
+int afc_serve_release(afc_server s, int64_t id);
+int afc_serve_get_info(afc_server s, afc_serve_info* out);
+/* Stops the threads (running solves finish), cancels pending requests, frees all. */
+int afc_serve_destroy(afc_server s);
+
 /* ---- diagnostics -------------------------------------------------------------- */
 
 /* Per-kernel device time of the library's launches on this problem.

@@ -32,6 +32,9 @@ AFC_KSP_BICGSTAB, AFC_KSP_GMRES = 0, 1
 AFC_FP64, AFC_MIXED = 0, 1
 AFC_MAT_MC, AFC_MAT_A, AFC_MAT_D, AFC_MAT_LOW, AFC_MAT_K, AFC_MAT_S = 0, 1, 2, 3, 4, 5
 AFC_BATCH_AUTO, AFC_BATCH_PER_PASS, AFC_BATCH_PER_STAGE, AFC_BATCH_PER_STEP = 0, 1, 2, 3
+AFC_REQ_TRANSIENT, AFC_REQ_STATIONARY = 0, 1
+AFC_SERVE_BATCHED, AFC_SERVE_SERIAL = 0, 1
+AFC_REQ_PENDING, AFC_REQ_RUNNING, AFC_REQ_DONE, AFC_REQ_FAILED, AFC_REQ_CANCELLED = 0, 1, 2, 3, 4
 
 ELEM = {"p1": AFC_P1, "q1": AFC_Q1}
 
@@ -58,6 +61,31 @@ class afc_stats(C.Structure):
 class afc_batch_tuning(C.Structure):
     _fields_ = [("mode", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("ms_per_step", C.c_double)]
+
+
+class afc_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("elem", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("eps", C.c_double), ("c", C.c_double),
+                ("b", C.POINTER(C.c_double)), ("f", C.POINTER(C.c_double)), ("dir_mask", C.POINTER(C.c_uint8)),
+                ("u_dir", C.POINTER(C.c_double)), ("u0", C.POINTER(C.c_double)), ("family", C.c_int32),
+                ("steps", C.c_int32), ("cfl", C.c_double), ("opts", afc_opts)]
+
+
+class afc_result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("stats", afc_stats), ("n_nodes", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("message", C.c_char * 160)]
+
+
+class afc_serve_config(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("max_active", C.c_int32), ("hbm_budget", C.c_int64),
+                ("stationary_workers", C.c_int32), ("max_chunk", C.c_int32)]
+
+
+class afc_serve_info(C.Structure):
+    _fields_ = [("pending", C.c_int64), ("active", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("completed", C.c_int64), ("failed", C.c_int64), ("chunks", C.c_int64),
+                ("batched_steps", C.c_int64), ("max_batch", C.c_int64), ("clock", C.c_double)]
 
 
 _P = C.c_void_p
@@ -98,6 +126,16 @@ _SIGS = {
     "afc_batch_get_tuning": (C.c_int, [_P, C.POINTER(afc_batch_tuning)]),
     "afc_batch_tune": (C.c_int, [_P, C.POINTER(afc_opts), _D, C.POINTER(afc_batch_tuning)]),
     "afc_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "afc_serve_default_config": (None, [C.POINTER(afc_serve_config)]),
+    "afc_serve_estimate_bytes": (C.c_int64, [C.POINTER(afc_request)]),
+    "afc_serve_create": (C.c_int, [C.c_int, C.POINTER(afc_serve_config), C.POINTER(_P)]),
+    "afc_serve_submit": (C.c_int, [_P, C.POINTER(afc_request), C.POINTER(C.c_int64)]),
+    "afc_serve_poll": (C.c_int, [_P, C.c_int64, C.POINTER(afc_result), _D]),
+    "afc_serve_wait": (C.c_int, [_P, C.c_int64, C.c_double, C.POINTER(afc_result), _D]),
+    "afc_serve_cancel": (C.c_int, [_P, C.c_int64]),
+    "afc_serve_release": (C.c_int, [_P, C.c_int64]),
+    "afc_serve_get_info": (C.c_int, [_P, C.POINTER(afc_serve_info)]),
+    "afc_serve_destroy": (C.c_int, [_P]),
     "afc_status_str": (C.c_char_p, [C.c_int]),
     "afc_last_error": (C.c_char_p, []),
 }
@@ -411,3 +449,121 @@ class Batch:
         tn, nl = C.c_int64(), C.c_int64()
         _check(_lib.afc_batch_info(self.h, C.byref(tn), C.byref(nl)), "afc_batch_info")
         return tn.value, nl.value
+
+
+def _struct_dict(x) -> dict:
+    out = {}
+    for name, _ in x._fields_:
+        v = getattr(x, name)
+        if isinstance(v, afc_stats):
+            v = stats_dict(v)
+        elif isinstance(v, bytes):
+            v = v.decode(errors="replace")
+        out[name] = v
+    return out
+
+
+def serve_config(**kw) -> afc_serve_config:
+    c = afc_serve_config()
+    _lib.afc_serve_default_config(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Request:
+    """An afc_request plus the arrays it points to (kept alive until submission)."""
+
+    def __init__(self, kind, elem, n, eps, c, b, u0, dir_mask, u_dir, f=None, opts=None, steps=0, cfl=0.5,
+                 family=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+        if np.isscalar(n):
+            n = (int(n),) * 3
+        N = int(np.prod(n))
+        self.N = N
+        self._b = _f64(np.broadcast_to(np.asarray(b, dtype=np.float64), (N, 3)), 3 * N)
+        self._u0 = _f64(u0, N)
+        self._m = np.ascontiguousarray(np.asarray(dir_mask, dtype=np.uint8))
+        self._ud = _f64(np.broadcast_to(np.asarray(u_dir, dtype=np.float64), (N,)), N)
+        self._f = None if f is None else _f64(np.broadcast_to(np.asarray(f, dtype=np.float64), (N,)), N)
+        r = afc_request()
+        r.kind = kind
+        r.elem = ELEM.get(elem, elem)
+        r.n[:] = [int(v) for v in n]
+        r.lo[:] = [float(v) for v in lo]
+        r.hi[:] = [float(v) for v in hi]
+        r.eps, r.c = float(eps), float(c)
+        r.b, r.u0, r.u_dir = _dp(self._b), _dp(self._u0), _dp(self._ud)
+        r.dir_mask = self._m.ctypes.data_as(_U8)
+        r.f = _dp(self._f) if self._f is not None else None
+        if family is None:
+            family = AFC_FAMILY_MC if kind == AFC_REQ_STATIONARY else AFC_FAMILY_FCT
+        r.family = family
+        r.steps = int(steps)
+        r.cfl = float(cfl)
+        r.opts = opts if opts is not None else default_opts()
+        self.c = r
+
+    def estimate_bytes(self) -> int:
+        return int(_lib.afc_serve_estimate_bytes(C.byref(self.c)))
+
+
+class Server:
+    """Owner of one afc_server handle."""
+
+    def __init__(self, device=0, **cfg):
+        c = serve_config(**cfg)
+        h = C.c_void_p()
+        _check(_lib.afc_serve_create(int(device), C.byref(c), C.byref(h)), "afc_serve_create")
+        self.h = h
+        self.sizes = {}
+
+    def close(self):
+        if self.h:
+            _lib.afc_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, req: Request) -> int:
+        rid = C.c_int64()
+        _check(_lib.afc_serve_submit(self.h, C.byref(req.c), C.byref(rid)), "afc_serve_submit")
+        self.sizes[rid.value] = req.N
+        return rid.value
+
+    def poll(self, rid, want_u=False):
+        res = afc_result()
+        u = np.zeros(self.sizes[rid]) if want_u else None
+        _check(_lib.afc_serve_poll(self.h, int(rid), C.byref(res), _dp(u) if u is not None else None),
+               "afc_serve_poll")
+        return _struct_dict(res), u
+
+    def wait(self, rid, timeout=-1.0, want_u=True):
+        res = afc_result()
+        u = np.zeros(self.sizes[rid]) if want_u else None
+        _check(_lib.afc_serve_wait(self.h, int(rid), float(timeout), C.byref(res),
+                                   _dp(u) if u is not None else None), "afc_serve_wait")
+        return _struct_dict(res), u
+
+    def cancel(self, rid):
+        _check(_lib.afc_serve_cancel(self.h, int(rid)), "afc_serve_cancel")
+
+    def release(self, rid):
+        _check(_lib.afc_serve_release(self.h, int(rid)), "afc_serve_release")
+        self.sizes.pop(rid, None)
+
+    def info(self) -> dict:
+        i = afc_serve_info()
+        _check(_lib.afc_serve_get_info(self.h, C.byref(i)), "afc_serve_get_info")
+        return _struct_dict(i)

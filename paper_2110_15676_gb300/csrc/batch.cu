@@ -579,7 +579,20 @@ void batch_free(afc_batch_s* b) {
 
 using namespace afc;
 
+namespace afc {
+
+// A batch enqueued on `stream` instead of the first problem's.
+int batch_create_on_stream(const afc_problem* list, int count, cudaStream_t stream, afc_batch* out);
+
+}  // namespace afc
+
 extern "C" int afc_batch_create(const afc_problem* list, int count, afc_batch* out) {
+  if (!out || !list) { set_error("null argument"); return AFC_E_INVALID; }
+  if (count < 1 || !list[0]) { set_error("batch size must be 1..65536"); return AFC_E_INVALID; }
+  return afc::batch_create_on_stream(list, count, list[0]->stream, out);
+}
+
+int afc::batch_create_on_stream(const afc_problem* list, int count, cudaStream_t stream, afc_batch* out) {
   if (!out || !list) { set_error("null argument"); return AFC_E_INVALID; }
   *out = nullptr;
   if (count < 1 || count > 65536) { set_error("batch size must be 1..65536"); return AFC_E_INVALID; }
@@ -593,7 +606,7 @@ extern "C" int afc_batch_create(const afc_problem* list, int count, afc_batch* o
   afc_batch_s* b = new afc_batch_s();
   b->list.assign(list, list + count);
   b->device = list[0]->device;
-  b->stream = list[0]->stream;
+  b->stream = stream;
   for (auto* p : b->list) b->total_nodes += p->N;
   auto fail = [&](int st) {
     batch_free(b);

@@ -17,6 +17,8 @@ constant convection, small diffusion, data in [0, 1]):
   z = 0 with value 1 where x = 0 and y < 0.5, else 0.
 * ``random_transient``: a seeded random instance (node count per side, eps,
   constant unit velocity, hump centre) for batched runs.
+* ``serving_mix``: a seeded mix of stationary and transient problems of random
+  size, element type, eps and c, for a request stream.
 """
 from __future__ import annotations
 
@@ -121,6 +123,28 @@ def random_transient(rng: np.random.Generator, elem: str = Q1, n_range=(17, 49))
         name=f"random_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
         eps=eps, c=0.0, b=np.tile(v, (N, 1)), f=np.zeros(N), u0=cosine_hump(xyz, center),
         dir_mask=boundary_mask(n), u_dir=np.zeros(N))
+
+
+def serving_mix(rng: np.random.Generator, count: int, n_range=(17, 97)) -> list:
+    """A request stream's problems: each is stationary (the inflow problem above)
+    or transient (a random_transient instance) with probability 1/2, on P1 or Q1
+    with probability 1/2, with n uniform in n_range, eps log-uniform in
+    [1e-8, 1e-4] and c uniform in [0, 1].  Returns (kind, Workload) pairs, kind
+    "stationary" or "transient"."""
+    out = []
+    for _ in range(count):
+        kind = "stationary" if rng.uniform() < 0.5 else "transient"
+        elem = P1 if rng.uniform() < 0.5 else Q1
+        if kind == "stationary":
+            n = int(rng.integers(n_range[0], n_range[1] + 1))
+            eps = float(10.0 ** rng.uniform(-8.0, -4.0))
+            c = float(rng.uniform(0.0, 1.0))
+            wl = stationary_inflow(elem, n, eps=eps, c=c)
+        else:
+            wl = random_transient(rng, elem, n_range)
+            wl.c = float(rng.uniform(0.0, 1.0))
+        out.append((kind, wl))
+    return out
 
 
 def random_field(rng: np.random.Generator, N: int, lo=0.0, hi=1.0) -> np.ndarray:
