@@ -158,10 +158,31 @@ def _timed_steps(P, opts, steps, flush, stream, torch):
     return ms_total, its_total, inner_total, statuses
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# (profiles/k_bicg_spmv2_q1_65.md), valid while the kernel's sources hash as they did then.
+_NCU_TRAFFIC = {
+    "k_bicg_spmv2": {"bytes": 64.21e6, "sha1": "f38092f2cdd2bcab",
+                     "sources": ("krylov.cu", "kernels_common.cuh", "afc_internal.h")},
+}
+
+
+def _traffic(name):
+    import hashlib
+    t = _NCU_TRAFFIC.get(name)
+    if t is None:
+        return None
+    h = hashlib.sha1()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_2110_15676_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest()[:16] == t["sha1"] else None
+
+
 def _roofline(name, kms, kcount, work_flops, share):
     achieved = work_flops / (kms / kcount / 1e3) / 1e12
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic(name),
+            "traffic_unit": "bytes per launch (ncu, cold cache)",
             "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit counts, max clock)",
             "avg_launch_us": kms / kcount * 1e3, "share": share}
 
