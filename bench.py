@@ -187,7 +187,33 @@ def _roofline(name, kms, kcount, work_flops, share):
             "avg_launch_us": kms / kcount * 1e3, "share": share}
 
 
-def mc_sweep(afc, W, torch, flush, stream, reps):
+def _mc_solve(afc, P, wl, torch, stream):
+    # the whole stationary MC solve of this workload (damped fixed point, omega = 0.5,
+    # tol 1e-10, mixed-precision Jacobi-GMRES(20) inner solves to a relative 1e-6)
+    sopts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0, ksp_rtol=1e-6,
+                             fp_tol=1e-10, fp_maxit=1000, precision=afc.AFC_MIXED)
+    P.set_solution(wl.u0)
+    P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
+                                        ksp_rtol=1e-6, fp_fixed_its=1, precision=afc.AFC_MIXED))   # build / warm
+    P.set_solution(wl.u0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sst = P.solve_stationary(sopts)
+    e1.record(stream)
+    e1.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    u_sol = P.get_solution()
+    N = P.info()["n_nodes"]
+    return {"ms": solve_ms, "fixed_point_its": sst["outer_its"], "gmres_its": sst["inner_its"],
+            "status": sst["status"], "res_final": sst["res_final"],
+            "dof_iters_per_s": N * sst["outer_its"] / (solve_ms / 1e3),
+            "umin": float(u_sol.min()), "umax": float(u_sol.max()),
+            "options": "omega 0.5, tol 1e-10, mixed: FP32 Jacobi-GMRES(20) rtol 1e-6, FP64 outer"}
+
+
+def mc_sweep(afc, W, torch, flush, stream, reps, solve=True):
     """The stationary MC limiter + residual sweep on Kuhn P1 129^3 (2,146,689 dofs):
     bounds, limited fluxes of all 14.8 M pairs, residual SpMV and norm, timed on the
     iterate after 6 damped fixed-point corrections from u0."""
@@ -223,23 +249,9 @@ def mc_sweep(afc, W, torch, flush, stream, reps):
     prof, _ = P.profile_read()
     P.profile(False)
     sweep_ms = ms / reps
-    # the whole stationary MC solve of this workload (damped fixed point, omega = 0.5,
-    # tol 1e-10, mixed-precision Jacobi-GMRES(20) inner solves to a relative 1e-6)
-    sopts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0, ksp_rtol=1e-6,
-                             fp_tol=1e-10, fp_maxit=1000, precision=afc.AFC_MIXED)
-    P.set_solution(wl.u0)
-    P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
-                                        ksp_rtol=1e-6, fp_fixed_its=1, precision=afc.AFC_MIXED))   # build / warm
-    P.set_solution(wl.u0)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sst = P.solve_stationary(sopts)
-    e1.record(stream)
-    e1.synchronize()
-    solve_ms = e0.elapsed_time(e1)
-    u_sol = P.get_solution()
+    solve_out = None
+    if solve:
+        solve_out = _mc_solve(afc, P, wl, torch, stream)
     # algorithmic work of one sweep (design notes): FP64 flops 14 per pair + 2 per entry;
     # bytes of the CSR count 4(N+1) + 12 nnz + 24 E + 24 N
     flops = 14.0 * E + 2.0 * nnz
@@ -254,11 +266,7 @@ def mc_sweep(afc, W, torch, flush, stream, reps):
                    "unit": "TFLOP/s", "frac": flops / (sweep_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                    "algorithmic_flops": flops},
            "kernels": {k: {"ms": v[0] / reps, "launches": v[1] // reps} for k, v in prof.items()},
-           "solve": {"ms": solve_ms, "fixed_point_its": sst["outer_its"], "gmres_its": sst["inner_its"],
-                     "status": sst["status"], "res_final": sst["res_final"],
-                     "dof_iters_per_s": N * sst["outer_its"] / (solve_ms / 1e3),
-                     "umin": float(u_sol.min()), "umax": float(u_sol.max()),
-                     "options": "omega 0.5, tol 1e-10, mixed: FP32 Jacobi-GMRES(20) rtol 1e-6, FP64 outer"}}
+           "solve": solve_out}
     del P
     return out
 
@@ -453,7 +461,7 @@ def run_ours(args, ws, rank, local):
     if args.only_mc_sweep:
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         print(json.dumps({"mc_sweep": mc_sweep(afc, W, torch, flush, torch.cuda.current_stream(),
-                                               max(args.steps, 1))}))
+                                               max(args.steps, 1), solve=not args.no_mc_solve)}))
         return
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -642,6 +650,7 @@ def main():
                     help="launch shape of the batched run (--only-batched); auto = tuned")
     ap.add_argument("--batched-block", type=int, default=128)
     ap.add_argument("--no-solo", action="store_true", help="skip the one-at-a-time path (--only-batched)")
+    ap.add_argument("--no-mc-solve", action="store_true", help="time the MC sweep but not the whole MC solve")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--only-serving", action="store_true", help="time only the request-server streams")
     ap.add_argument("--serving-count", type=int, default=48)
