@@ -632,7 +632,8 @@ int afc::batch_create_on_stream(const afc_problem* list, int count, cudaStream_t
     set_error("device allocation of the batch tables failed");
     return fail(AFC_E_OOM);
   }
-  if ((e = cudaMemset(b->bar, 0, sizeof(GridBar))) != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
+  if ((e = cudaMemsetAsync(b->bar, 0, sizeof(GridBar), b->stream)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMemsetAsync"));
   *out = b;
   return AFC_OK;
 }

@@ -50,6 +50,18 @@ __device__ __forceinline__ double neg_bits(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
 }
 
+// Exact float -> double on the integer pipe (zero and subnormal floats give a
+// signed zero; every user of a flux widens it the same way, so P+/- and F* see
+// the same values).
+__device__ __forceinline__ double widen_exact(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned long long de = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  const unsigned long long bits = e == 0u ? s : (s | (de << 52) | ((unsigned long long)(b & 0x7fffffu) << 29));
+  return __longlong_as_double((long long)bits);
+}
+
 // min / max of two values known to be >= 0 (correction factors, bounds): plain int compare
 __device__ __forceinline__ double imin_nn(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
@@ -101,19 +113,43 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Sum v over the block (fixed order) and store it in part[blockIdx.x].
-// Every thread of the block must call it.
+// Block sums in a fixed order.  On GB300 every FP64 warp instruction costs the
+// FP64 pipe 16 cycles whatever its active lanes, so a shuffle tree in every warp
+// (5 adds per warp) is the expensive way to sum a block.  Instead every thread
+// stores its value in shared memory and warp 0 alone sums them: each lane adds
+// blockDim/32 values, then one shuffle tree (blockDim/32 - 1 + 5 adds per block
+// instead of 5 per warp).  Blocks of more than kBlock threads take the shuffle
+// route.  Every thread of the block must call these.
+__device__ __forceinline__ double warp0_column_sum(const double* col) {
+  const int lane = threadIdx.x;   // < 32
+  double t = col[lane];
+  for (int w = lane + 32; w < (int)blockDim.x; w += 32) t += col[w];
+  return warp_sum(t);
+}
+
+// Sum v over the block and store it in part[blockIdx.x].
 __device__ __forceinline__ void block_sum_to(double v, double* part) {
-  __shared__ double sh[32];
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = v;
+  __shared__ double sh[kBlock];
+  if (blockDim.x > kBlock) {
+    __shared__ double sw[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sw[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+      double t = lane < nw ? sw[lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) part[blockIdx.x] = t;
+    }
+    __syncthreads();
+    return;
+  }
+  sh[threadIdx.x] = v;
   __syncthreads();
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    double t = lane < nw ? sh[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) part[blockIdx.x] = t;
+  if (threadIdx.x < 32) {
+    const double t = warp0_column_sum(sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
   }
   __syncthreads();
 }
@@ -121,21 +157,20 @@ __device__ __forceinline__ void block_sum_to(double v, double* part) {
 // Several sums at once (NV values per thread), stored at part[q * stride + blockIdx.x].
 template <int NV>
 __device__ __forceinline__ void block_sums_to(double (&v)[NV], double* part, int64_t stride) {
-  __shared__ double sh[NV][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (blockDim.x > kBlock) {
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    double t = warp_sum(v[q]);
-    if (lane == 0) sh[q][w] = t;
+    for (int q = 0; q < NV; ++q) block_sum_to(v[q], part + q * stride);
+    return;
   }
+  __shared__ double sh[NV][kBlock];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = v[q];
   __syncthreads();
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x < 32) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double t = lane < nw ? sh[q][lane] : 0.0;
-      t = warp_sum(t);
-      if (lane == 0) part[q * stride + blockIdx.x] = t;
+      const double t = warp0_column_sum(sh[q]);
+      if (threadIdx.x == 0) part[q * stride + blockIdx.x] = t;
     }
   }
   __syncthreads();

@@ -32,8 +32,11 @@ int DBuf<T>::alloc(int64_t n_, int64_t pad_) {
     set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
     return AFC_E_OOM;
   }
-  e = cudaMemset(base, 0, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  // zero-fill and wait for it here: a plain cudaMemset runs on the legacy default
+  // stream, which is not ordered with the non-blocking streams a problem may use
+  e = cudaMemsetAsync(base, 0, bytes, cudaStreamPerThread);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   n = n_;
   pad = pad_;
   p = base + pad_;
@@ -215,17 +218,27 @@ namespace {
 // sees a scalar that the same kernel changes.
 // Sum v over the block in a fixed order; every thread receives the total.
 __device__ __forceinline__ double block_allsum(double v) {
-  __shared__ double sh[32];
   __shared__ double total;
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    double t = lane < nw ? sh[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) total = t;
+  if (blockDim.x > kBlock) {
+    __shared__ double sw[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sw[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+      double t = lane < nw ? sw[lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) total = t;
+    }
+  } else {
+    __shared__ double sh[kBlock];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const double t = warp0_column_sum(sh);
+      if (threadIdx.x == 0) total = t;
+    }
   }
   __syncthreads();
   const double r = total;

@@ -51,7 +51,10 @@ __global__ void k_mc_bounds(int64_t N, Offsets of, const unsigned long long* __r
   const double A = hi - ui, B = ui - lo;
   bA[i] = A;
   bB[i] = B;
-  nf[i] = make_float4((float)ui, (float)A, (float)B, 0.f);   // rounded copies for the pre-test
+  // rounded copies for the pre-test; w = 1 where the single copy of u is exact
+  const float uf = __double2float_rn(ui);
+  const bool exact = __double_as_longlong(widen_exact(uf)) == __double_as_longlong(ui);
+  nf[i] = make_float4(uf, (float)A, (float)B, exact ? 1.f : 0.f);
   clip[i] = 0u;
 }
 
@@ -95,6 +98,7 @@ __global__ void k_mc_edges(int64_t N, Offsets of, const double* __restrict__ d2_
   const bool side_i = cf.y > 0.f, side_j = cf.z > 0.f;
   if (!(cf.x > 0.f) || !(side_i || side_j)) return;   // d = 0, or no side can clip
   const float4 ni = nf[i], nj = nf[j];
+  if (ni.x == nj.x && ni.w != 0.f && nj.w != 0.f) return;   // equal exact copies: u_i = u_j, r = 0
   if (ni.x != nj.x) {   // equal single copies need not mean equal values: decided in double below
     const bool rpos = nj.x < ni.x;
     const bool ok_i = !side_i || side_certainly_unclipped(cf.x, cf.y, rpos ? ni.y : ni.z, ni.x, nj.x);

@@ -21,18 +21,6 @@
 
 namespace afc {
 
-// Exact float -> double on the integer pipe (zero and subnormal floats give a
-// signed zero; every user of a flux widens it the same way, so P+/- and F* see
-// the same values).
-__device__ __forceinline__ double widen_exact(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned e = (b >> 23) & 0xffu;
-  const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
-  const unsigned long long de = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
-  const unsigned long long bits = e == 0u ? s : (s | (de << 52) | ((unsigned long long)(b & 0x7fffffu) << 29));
-  return __longlong_as_double((long long)bits);
-}
-
 // Flux of the pair (i, i + o_k) seen from row i, stored once per pair as a float.
 __device__ __forceinline__ double pair_flux32(const Offsets& of, int Kup, int k, int64_t i, int64_t N,
                                               const float* __restrict__ r32) {
