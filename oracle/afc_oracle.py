@@ -49,6 +49,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 P1 = "p1"
 Q1 = "q1"
@@ -417,8 +418,11 @@ def cn_step(prob: Problem, u_old, dt, tol=1e-10, max_outer=100, omega=1.0, preli
                 break
         elif it == fixed_iterations:
             break
-        delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
-        stats["inner_its"] += kst["its"]
+        if lu is not None:
+            delta = lu.solve(res)
+        else:
+            delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
+            stats["inner_its"] += kst["its"]
         u = u + omega * delta
         stats["outer_its"] += 1
     stats["res_final"] = stats["res_hist"][-1]
@@ -476,13 +480,15 @@ def mc_stationary(prob: Problem, u0=None, tol=1e-10, max_outer=1000, omega=0.5, 
                   fixed_iterations=None):
     """Sec. 3.1 with the damped fixed point of Sec. 4 (reading A5):
     res = f + F*(u) - AA u, AA delta = res, u <- u + omega delta,
-    stop when ||res||_2 < sqrt(N) tol."""
+    stop when ||res||_2 < sqrt(N) tol.  ksp = "direct" solves AA delta = res with a
+    sparse LU factorisation computed once (AA does not change between iterations)."""
     N = prob.mesh.n_nodes
     dirm = prob.dir_mask
     u = np.zeros(N) if u0 is None else np.array(u0, dtype=np.float64)
     u[dirm] = prob.u_dir[dirm]
     Bsys = stationary_system_matrix(prob)
     dinv = 1.0 / Bsys.diagonal()
+    lu = spla.splu(Bsys.tocsc()) if ksp == "direct" else None   # factor once: the matrix is fixed
     stats = dict(outer_its=0, inner_its=0, res_hist=[])
     for it in range(max_outer + 1):
         rstar, _ = mc_limited_fluxes(prob, u, mode)
@@ -496,8 +502,11 @@ def mc_stationary(prob: Problem, u0=None, tol=1e-10, max_outer=1000, omega=0.5, 
                 break
         elif it == fixed_iterations:
             break
-        delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
-        stats["inner_its"] += kst["its"]
+        if lu is not None:
+            delta = lu.solve(res)
+        else:
+            delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
+            stats["inner_its"] += kst["its"]
         u = u + omega * delta
         stats["outer_its"] += 1
     stats["res_final"] = stats["res_hist"][-1]
@@ -619,3 +628,48 @@ def gmres(B, b, dinv, m=20, atol=1e-12, rtol=0.0, maxit=1000):
 def dense_solve(B, b):
     """Direct solve for tiny systems (Gaussian elimination with partial pivoting)."""
     return np.linalg.solve(B.toarray(), b)
+
+
+# --------------------------------------------------------------------------
+# Error norms of a P1 solution (the L1 and L2 errors the circular convection
+# example reports)
+# --------------------------------------------------------------------------
+def conical_rule(nq: int):
+    """Conical product quadrature on the reference tetrahedron (Stroud): Gauss-
+    Legendre points s1, s2, s3 in [0, 1], x = s1, y = s2 (1 - s1),
+    z = s3 (1 - s1)(1 - s2), weight w1 w2 w3 (1 - s1)^2 (1 - s2).  Returns the
+    barycentric coordinates (nq^3, 4) and weights summing to 1/6."""
+    g, w = np.polynomial.legendre.leggauss(nq)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    S1, S2, S3 = np.meshgrid(g, g, g, indexing="ij")
+    W = (w[:, None, None] * w[None, :, None] * w[None, None, :]).ravel()
+    s1, s2, s3 = S1.ravel(), S2.ravel(), S3.ravel()
+    x = s1
+    y = s2 * (1.0 - s1)
+    z = s3 * (1.0 - s1) * (1.0 - s2)
+    W = W * (1.0 - s1) ** 2 * (1.0 - s2)
+    lam = np.stack([1.0 - x - y - z, x, y, z], axis=1)
+    return lam, W
+
+
+def p1_error_norms(mesh: Mesh, uh, exact, nq: int = 4, chunk: int = 20000):
+    """(||u - u_h||_{L1}, ||u - u_h||_{L2}) over the tetrahedra of `mesh`, u_h the
+    piecewise linear interpolant of the nodal values uh and exact(x, y, z) the
+    exact solution, by the conical rule with nq^3 points per tetrahedron."""
+    if mesh.elem != P1:
+        raise ValueError("P1 meshes only")
+    lam, W = conical_rule(nq)
+    uh = np.asarray(uh, dtype=np.float64)
+    e1 = 0.0
+    e2 = 0.0
+    for s in range(0, len(mesh.cells), chunk):
+        c = mesh.cells[s:s + chunk]
+        X = mesh.xyz[c]                                          # (E, 4, 3)
+        six_vol = np.abs(np.linalg.det(X[:, 1:] - X[:, :1]))    # |det| = 6 V
+        P = np.einsum("qk,ekd->eqd", lam, X)
+        Uh = np.einsum("qk,ek->eq", lam, uh[c])
+        d = np.abs(Uh - exact(P[..., 0], P[..., 1], P[..., 2]))
+        e1 += float((d * W[None]).sum(axis=1) @ six_vol)
+        e2 += float((d * d * W[None]).sum(axis=1) @ six_vol)
+    return e1, math.sqrt(e2)

@@ -17,6 +17,9 @@ constant convection, small diffusion, data in [0, 1]):
   z = 0 with value 1 where x = 0 and y < 0.5, else 0.
 * ``random_transient``: a seeded random instance (node count per side, eps,
   constant unit velocity, hump centre) for batched runs.
+* ``circular_convection``: the paper's circular convection example (eps = 0,
+  b = (y, -x, 0), exact solution ``circular_exact`` as Dirichlet data on the
+  faces y = 1, x = 0, x = 1) on the Kuhn P1 grid.
 * ``serving_mix``: a seeded mix of stationary and transient problems of random
   size, element type, eps and c, for a request stream.
 """
@@ -123,6 +126,37 @@ def random_transient(rng: np.random.Generator, elem: str = Q1, n_range=(17, 49))
         name=f"random_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
         eps=eps, c=0.0, b=np.tile(v, (N, 1)), f=np.zeros(N), u0=cosine_hump(xyz, center),
         dir_mask=boundary_mask(n), u_dir=np.zeros(N))
+
+
+def circular_exact(x, y) -> np.ndarray:
+    """Exact solution of the circular convection example: with r = sqrt(x^2 + y^2),
+    1 on 0.15 <= r <= 0.45, cos^2(10 pi (r - 0.7) / 3) on 0.55 <= r <= 0.85, else 0."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    r = np.sqrt(x * x + y * y)
+    u = np.zeros_like(r)
+    u[(r >= 0.15) & (r <= 0.45)] = 1.0
+    ring = (r >= 0.55) & (r <= 0.85)
+    u[ring] = np.cos(10.0 * np.pi * (r[ring] - 0.7) / 3.0) ** 2
+    return u
+
+
+def circular_convection(n: int) -> Workload:
+    """The paper's circular convection example on the Kuhn P1 grid with n nodes per
+    side: unit cube, eps = 0, b = (y, -x, 0), c = 0, f = 0, Dirichlet data (the exact
+    solution) on the faces y = 1, x = 0 and x = 1, homogeneous Neumann elsewhere;
+    initial guess 0 with the Dirichlet values."""
+    xyz = grid_coords(n)
+    N = len(xyz)
+    ix, iy, iz = grid_index(n)
+    x, y = xyz[:, 0], xyz[:, 1]
+    dirm = (iy == n - 1) | (ix == 0) | (ix == n - 1)
+    u_dir = circular_exact(x, y)
+    b = np.stack([y, -x, np.zeros(N)], axis=1)
+    return Workload(
+        name=f"circular_p1_{n}^3", elem=P1, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
+        eps=0.0, c=0.0, b=b, f=np.zeros(N), u0=np.where(dirm, u_dir, 0.0),
+        dir_mask=dirm.astype(np.uint8), u_dir=u_dir)
 
 
 def serving_mix(rng: np.random.Generator, count: int, n_range=(17, 97)) -> list:

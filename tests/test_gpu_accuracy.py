@@ -1,0 +1,54 @@
+"""The CUDA path on the paper's circular convection example (MC limiter, stationary,
+Kuhn P1 levels 5 and 6): errors equal the oracle's at level 5, are of the printed
+order at both levels, and decrease with refinement."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import afc_oracle as O
+from paper_2110_15676_gb300 import workloads as W
+from pairs import gpu_problem
+from test_oracle_accuracy import printed_errors, stored_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_errors(level, precision):
+    from paper_2110_15676_gb300 import afc
+    n = 2 ** level + 1
+    wl = W.circular_convection(n)
+    g = gpu_problem(wl.elem, wl.n, wl.b, wl.eps, wl.c, wl.f, wl.dir_mask, wl.u_dir, family="mc",
+                    precision=precision)
+    g.set_solution(wl.u0)
+    mixed = precision == "mixed"
+    opts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
+                            ksp_rtol=1e-6 if mixed else 1e-10, fp_tol=1e-13, fp_maxit=6000,
+                            precision=afc.AFC_MIXED if mixed else afc.AFC_FP64)
+    st = g.solve_stationary(opts)
+    u = g.get_solution()
+    g.close()
+    mesh = O.structured_mesh("p1", n)
+    e1, e2 = O.p1_error_norms(mesh, u, lambda X, Y, Z: W.circular_exact(X, Y), nq=4 if level <= 5 else 3)
+    return st, u, e1, e2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_circular_convection_level5_equals_oracle(precision):
+    st, u, e1, e2 = gpu_errors(5, precision)
+    assert st["status"] == 0, st
+    s1, s2 = stored_oracle()[5]
+    assert abs(e1 - s1) < 1e-6 * s1 and abs(e2 - s2) < 1e-6 * s2, (e1, e2, s1, s2)
+    assert u.min() >= -1e-14 and u.max() <= 1.0 + 1e-14
+
+
+def test_circular_convection_level6_printed_order_and_convergence():
+    ref = printed_errors()
+    st6, u6, a1, a2 = gpu_errors(6, "mixed")
+    assert st6["status"] == 0, st6
+    _, p1, p2 = ref[6]
+    assert 0.7 * p1 <= a1 <= 1.3 * p1, a1
+    assert 0.7 * p2 <= a2 <= 1.3 * p2, a2
+    s1, s2 = stored_oracle()[5]
+    assert a1 < s1 and a2 < s2
+    assert u6.min() >= -1e-14 and u6.max() <= 1.0 + 1e-14
