@@ -402,6 +402,7 @@ def cn_step(prob: Problem, u_old, dt, tol=1e-10, max_outer=100, omega=1.0, preli
     b0 = prob.mL / dt * u_old - 0.5 * (prob.AA @ u_old) + prob.f     # (f^n + f^{n-1})/2 = f
     Bsys = cn_system_matrix(prob, dt)
     dinv = 1.0 / Bsys.diagonal()
+    lu = spla.splu(Bsys.tocsc()) if ksp == "direct" else None   # factor once: the matrix is fixed
     u = u_old.copy()
     u[dirm] = prob.u_dir[dirm]
     stats = dict(outer_its=0, inner_its=0, res_hist=[])
