@@ -52,8 +52,13 @@ typedef enum { AFC_P1 = 0, AFC_Q1 = 1 } afc_elem;     /* tetrahedra / trilinear 
  *      D from the convective matrix K, AA = K + D + eps*S + c*M_L (lumped reaction). */
 typedef enum { AFC_FAMILY_FCT = 0, AFC_FAMILY_MC = 1 } afc_family;
 
-typedef enum { AFC_SSP2 = 0, AFC_SSP3 = 1, AFC_CN_NONLINEAR = 2 } afc_scheme;
-typedef enum { AFC_LIM_NONE = 0, AFC_LIM_GALERKIN = 1, AFC_LIM_ZALESAK = 2, AFC_LIM_MC = 3 } afc_limiter;
+typedef enum { AFC_SSP2 = 0, AFC_SSP3 = 1, AFC_CN_NONLINEAR = 2, AFC_CN_LINEAR = 3 } afc_scheme;
+/* Limiters: alpha = 0 (NONE), alpha = 1 (GALERKIN), Zalesak's (Sec. 2.1.3, FCT
+ * schemes), monolithic convex (Eq. MClimiter) and monolithic upwind (Sec. 3, MU
+ * limiter; stationary problems, MC family). */
+typedef enum {
+  AFC_LIM_NONE = 0, AFC_LIM_GALERKIN = 1, AFC_LIM_ZALESAK = 2, AFC_LIM_MC = 3, AFC_LIM_MU = 4
+} afc_limiter;
 typedef enum { AFC_KSP_BICGSTAB = 0, AFC_KSP_GMRES = 1 } afc_ksp;
 typedef enum { AFC_FP64 = 0, AFC_MIXED = 1 } afc_precision;
 
@@ -171,13 +176,20 @@ void afc_default_opts(afc_opts* o);
  *  AFC_CN_NONLINEAR: Eq. CNZal solved by the damped fixed point of Sec. 4 with
  *    fluxes Eq. flux_002 (+ Eq. prelimiting if opts->prelimit), the predictor
  *    Eq. forward_euler and a Jacobi-preconditioned Krylov solve per iteration.
+ *    With limiter AFC_LIM_MC (MC family, FP64) each stage is the transient MC
+ *    update of Sec. 2.2: the fluxes Eq. defn_r_ij_SSP clipped by Eq. MClimiter
+ *    with the bounds and bar states of the stage input.
+ *  AFC_CN_LINEAR: linear Zal+CN (Sec. 2.1.1): u^n in Eq. flux_002 is replaced by
+ *    2 u~ - u^{n-1}, so F* is known before the step and Eq. CNZal is one linear
+ *    system, solved by one Krylov solve (fp_tol, fp_maxit, omega are not used).
  * Returns AFC_NOT_CONVERGED (solution updated with the last iterate) if the
  * fixed point did not reach fp_tol within fp_maxit. */
 int afc_step(afc_problem p, const afc_opts* o, afc_stats* st);
 
 /* Stationary AFC system AA u = f + F*(u) (Sec. 3, Sec. 3.1) with the MC limiter
- * (Eq. MClimiter) or alpha = 1 / alpha = 0, by the damped fixed point of Sec. 4
- * in defect form, starting from the stored solution. */
+ * (Eq. MClimiter), the MU limiter (Sec. 3, MU limiter) or alpha = 1 / alpha = 0,
+ * by the damped fixed point of Sec. 4 in defect form, starting from the stored
+ * solution.  Needs the MC family assembly for any limiter but NONE. */
 int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* st);
 
 /* ---- single passes, for parity checks and diagnostics (host arrays) -------- */
@@ -194,8 +206,10 @@ int afc_fe_stage(afc_problem p, double dt, int limiter, double* u_tilde, double*
 int afc_cn_limited_sum(afc_problem p, double dt, int limiter, int prelimit, const double* u_new,
                        const double* u_old, double* u_tilde, double* Rp, double* Rm, double* Fstar);
 
-/* MC limited sum F*_i = sum_j r*_ij for a given u (host, N), with the bounds
- * u_max / u_min of Eq. u_max_min (outputs may be NULL). */
+/* Limited sum F*_i = sum_j alpha_ij r_ij of the stationary fluxes r_ij = d_ij (u_j - u_i)
+ * for a given u (host, N): MC (Eq. MClimiter, with the bounds u_max / u_min of
+ * Eq. u_max_min), MU (Sec. 3, MU limiter; u_max / u_min not written), GALERKIN or
+ * NONE (outputs may be NULL). */
 int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax, double* umin,
                        double* Fstar);
 

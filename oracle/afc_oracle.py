@@ -338,18 +338,38 @@ def fe_ssp_stage(prob: Problem, u, dt, mode="zalesak", want=False):
     return u_new
 
 
+def fe_mc_stage(prob: Problem, u, dt, want=False):
+    """One forward-Euler stage of the transient MC scheme (Sec. 2.2): the fluxes of
+    Eq. defn_r_ij_SSP with the low-order rate, limited by Eq. MClimiter with the
+    bounds and bar states of the stage input u, F*_i = sum_j r*_ij and
+    u_new = u + dt M_L^{-1}(f + F* - AA u), u_D on Dirichlet nodes (MC family)."""
+    udot = low_order_rate(prob, u)
+    r = ssp_fluxes(prob, u, udot)
+    rstar, lim = mc_clip(prob, u, r)
+    Fstar = limited_sum(prob, np.ones_like(rstar), rstar)
+    u_new = u + dt * (prob.f + Fstar - prob.AA @ u) / prob.mL
+    u_new[prob.dir_mask] = prob.u_dir[prob.dir_mask]
+    if want:
+        return u_new, dict(udot=udot, rstar=rstar, Fstar=Fstar, **lim)
+    return u_new
+
+
 def ssp_step(prob: Problem, u, dt, order=3, mode="zalesak"):
     """order 2: Heun's method as written in Sec. 2.1.2, u^n = (u^{n,0} + u^{n,2}) / 2.
     order 3: the three-stage Shu-Osher SSP scheme (reading A1), each stage one
-    forward-Euler FCT update."""
+    forward-Euler FCT update (mode "mc": one forward-Euler MC stage)."""
+    if mode == "mc":
+        stage = lambda v: fe_mc_stage(prob, v, dt)  # noqa: E731
+    else:
+        stage = lambda v: fe_ssp_stage(prob, v, dt, mode)  # noqa: E731
     if order == 2:
-        u1 = fe_ssp_stage(prob, u, dt, mode)
-        u2 = fe_ssp_stage(prob, u1, dt, mode)
+        u1 = stage(u)
+        u2 = stage(u1)
         return 0.5 * (u + u2)
     if order == 3:
-        u1 = fe_ssp_stage(prob, u, dt, mode)
-        u2 = 0.75 * u + 0.25 * fe_ssp_stage(prob, u1, dt, mode)
-        return u / 3.0 + (2.0 / 3.0) * fe_ssp_stage(prob, u2, dt, mode)
+        u1 = stage(u)
+        u2 = 0.75 * u + 0.25 * stage(u1)
+        return u / 3.0 + (2.0 / 3.0) * stage(u2)
     raise ValueError(order)
 
 
@@ -385,6 +405,33 @@ def cn_system_matrix(prob: Problem, dt):
     for i in np.flatnonzero(prob.dir_mask):
         B.rows[i] = [i]; B.data[i] = [1.0]
     return B.tocsr()
+
+
+def cn_linear_step(prob: Problem, u_old, dt, prelimit=True, mode="zalesak", ksp="direct", ksp_atol=1e-12,
+                   ksp_rtol=0.0, ksp_maxit=1000, gmres_restart=20):
+    """One step of linear Zal+CN (Sec. 2.1.1, the linearised scheme): u^n in the flux
+    formula Eq. flux_002 (and in the prelimiting of reading A3) is replaced by
+    2 u~ - u^{n-1}, u~ the predictor Eq. forward_euler, so the fluxes and the factors
+    are known before the step and Eq. CNZal becomes one linear system
+    (M_L/dt + AA/2) u^n = b0 + F*, Dirichlet rows u^n = u_D.  Returns (u_new, stats)."""
+    dirm = prob.dir_mask
+    u_tilde = u_old - 0.5 * dt * (prob.AA @ u_old - prob.f) / prob.mL
+    u_tilde[dirm] = prob.u_dir[dirm]
+    b0 = prob.mL / dt * u_old - 0.5 * (prob.AA @ u_old) + prob.f
+    u_approx = 2.0 * u_tilde - u_old
+    r = cn_fluxes(prob, u_approx, u_old, dt, prelimit)
+    alpha, _ = zalesak_limiter(prob, r, u_tilde, dt, mode)
+    Fstar = limited_sum(prob, alpha, r)
+    rhs = b0 + Fstar
+    rhs[dirm] = prob.u_dir[dirm]
+    Bsys = cn_system_matrix(prob, dt)
+    if ksp == "direct":
+        u = spla.splu(Bsys.tocsc()).solve(rhs)
+        its = 0
+    else:
+        u, kst = krylov_solve(Bsys, rhs, 1.0 / Bsys.diagonal(), ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
+        its = kst["its"]
+    return u, dict(outer_its=1, inner_its=its, Fstar=Fstar, u_tilde=u_tilde)
 
 
 def cn_step(prob: Problem, u_old, dt, tol=1e-10, max_outer=100, omega=1.0, prelimit=True,
@@ -449,13 +496,21 @@ def mc_limited_fluxes(prob: Problem, u, mode="mc"):
     entries (A8).  Returns r*_ij on the directed pairs and the bounds."""
     I, J = prob.pairs
     d = entries(prob.D, I, J)
-    aij = entries(prob.K, I, J)
-    aji = entries(prob.K, J, I)
     r = d * (u[J] - u[I])
     if mode == "galerkin":
         return r, {}
     if mode == "none":
         return np.zeros_like(r), {}
+    return mc_clip(prob, u, r)
+
+
+def mc_clip(prob: Problem, u, r):
+    """Eq. MClimiter applied to given fluxes r_ij on the directed pairs, with the
+    bounds Eq. u_max_min and the bar states of the state u."""
+    I, J = prob.pairs
+    d = entries(prob.D, I, J)
+    aij = entries(prob.K, I, J)
+    aji = entries(prob.K, J, I)
     umax, umin = mc_bounds(prob, u)
     rstar = np.zeros_like(r)
     nz = d != 0.0                                        # A16
@@ -467,6 +522,53 @@ def mc_limited_fluxes(prob: Problem, u, mode="mc"):
     dn = np.maximum(rr, np.maximum(2.0 * dI * (ubar_ij - umin[I[nz]]), 2.0 * dI * (umax[J[nz]] - ubar_ji)))
     rstar[nz] = np.where(rr > 0.0, up, dn)
     return rstar, dict(umax=umax, umin=umin, r=r)
+
+
+def mu_limited_fluxes(prob: Problem, u):
+    """Monolithic upwind limiter (Sec. 3, MU limiter) on the stationary fluxes
+    r_ij = d_ij (u_j - u_i), a_ij the convective entries (A8):
+      1. P_i^+/- = sum of r_ij^+/- over the j with a_ji <= a_ij,
+      2. Q_i^+ = -sum_j r_ij^-,  Q_i^- = -sum_j r_ij^+  (all neighbours),
+      3. R_i^+/- = min{1, Q_i^+/- / P_i^+/-}, 1 at Dirichlet nodes or where P = 0,
+      4. for a_ji <= a_ij: alpha_ij = R_i^+ (r_ij > 0), 1 (r_ij = 0), R_i^- (r_ij < 0),
+         and alpha_ji = alpha_ij.
+    A pair with a_ij = a_ji would be assigned from both ends; it is taken by the
+    end with the smaller index, in steps 1 and 4 alike (reading A21).  a_ij and a_ji
+    are computed values, so they count as equal within 1e-12 (|a_ij| + |a_ji|):
+    pairs that tie exactly in exact arithmetic stay ties after rounding.  Returns
+    alpha_ij r_ij on the directed pairs and the factors."""
+    I, J = prob.pairs
+    d = entries(prob.D, I, J)
+    aij = entries(prob.K, I, J)
+    aji = entries(prob.K, J, I)
+    r = d * (u[J] - u[I])
+    N = prob.mesh.n_nodes
+    tie = np.abs(aij - aji) <= 1e-12 * (np.abs(aij) + np.abs(aji))
+    owns = np.where(tie, I < J, aji < aij)               # i takes the pair (i, j)
+    rp = np.maximum(r, 0.0)
+    rm = np.minimum(r, 0.0)
+    Pp = np.zeros(N); Pm = np.zeros(N); Qp = np.zeros(N); Qm = np.zeros(N)
+    np.add.at(Pp, I[owns], rp[owns])
+    np.add.at(Pm, I[owns], rm[owns])
+    np.add.at(Qp, I, -rm)
+    np.add.at(Qm, I, -rp)
+    Rp = np.ones(N); Rm = np.ones(N)
+    nzp = Pp != 0.0
+    nzm = Pm != 0.0
+    with np.errstate(over="ignore"):                     # Q / P may exceed the range: R = 1 then
+        Rp[nzp] = np.minimum(1.0, Qp[nzp] / Pp[nzp])
+        Rm[nzm] = np.minimum(1.0, Qm[nzm] / Pm[nzm])
+    Rp[prob.dir_mask] = 1.0
+    Rm[prob.dir_mask] = 1.0
+    # alpha of the directed pair (i, j) as seen by the pair's owner
+    alpha_own = np.where(r > 0.0, Rp[I], np.where(r < 0.0, Rm[I], 1.0))
+    # the owner's value for each directed pair: (i, j) owned by i, else by j (the reverse pair)
+    order = np.lexsort((J, I))
+    key = I.astype(np.int64) * N + J
+    rev = np.searchsorted(key[order], J.astype(np.int64) * N + I)
+    rev_idx = order[rev]
+    alpha = np.where(owns, alpha_own, alpha_own[rev_idx])
+    return alpha * r, dict(Pp=Pp, Pm=Pm, Qp=Qp, Qm=Qm, Rp=Rp, Rm=Rm, alpha=alpha, r=r)
 
 
 def stationary_system_matrix(prob: Problem):
@@ -492,7 +594,10 @@ def mc_stationary(prob: Problem, u0=None, tol=1e-10, max_outer=1000, omega=0.5, 
     lu = spla.splu(Bsys.tocsc()) if ksp == "direct" else None   # factor once: the matrix is fixed
     stats = dict(outer_its=0, inner_its=0, res_hist=[])
     for it in range(max_outer + 1):
-        rstar, _ = mc_limited_fluxes(prob, u, mode)
+        if mode == "mu":
+            rstar, _ = mu_limited_fluxes(prob, u)
+        else:
+            rstar, _ = mc_limited_fluxes(prob, u, mode)
         Fstar = limited_sum(prob, np.ones_like(rstar), rstar)
         res = prob.f + Fstar - prob.AA @ u
         res[dirm] = 0.0

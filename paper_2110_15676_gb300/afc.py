@@ -26,8 +26,8 @@ AFC_OK, AFC_NOT_CONVERGED = 0, 1
 AFC_E_INVALID, AFC_E_OOM, AFC_E_CUDA, AFC_E_NAN, AFC_E_TIMEOUT, AFC_E_STATE = -1, -2, -3, -4, -5, -6
 AFC_P1, AFC_Q1 = 0, 1
 AFC_FAMILY_FCT, AFC_FAMILY_MC = 0, 1
-AFC_SSP2, AFC_SSP3, AFC_CN_NONLINEAR = 0, 1, 2
-AFC_LIM_NONE, AFC_LIM_GALERKIN, AFC_LIM_ZALESAK, AFC_LIM_MC = 0, 1, 2, 3
+AFC_SSP2, AFC_SSP3, AFC_CN_NONLINEAR, AFC_CN_LINEAR = 0, 1, 2, 3
+AFC_LIM_NONE, AFC_LIM_GALERKIN, AFC_LIM_ZALESAK, AFC_LIM_MC, AFC_LIM_MU = 0, 1, 2, 3, 4
 AFC_KSP_BICGSTAB, AFC_KSP_GMRES = 0, 1
 AFC_FP64, AFC_MIXED = 0, 1
 AFC_MAT_MC, AFC_MAT_A, AFC_MAT_D, AFC_MAT_LOW, AFC_MAT_K, AFC_MAT_S = 0, 1, 2, 3, 4, 5

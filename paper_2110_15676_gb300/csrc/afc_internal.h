@@ -181,11 +181,14 @@ struct SspArrays;
 SspArrays ssp_arrays(afc_problem_s* p);
 // CN helpers
 int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
+int cn_linear_guess(afc_problem_s* p, const double* u_old, double* u);             // u = 2 ut - u_old (after cn_predictor)
 // a = u - u_old, s = u + u_old after u += omega * delta (delta may be null)
 int cn_update(afc_problem_s* p, double omega, const double* delta, double* u, const double* u_old);
 int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int limiter, int prelimit, double* res,
                         double* normsq_slot);                                      // needs cn_update first
 // MC
+// transient MC stage: bounds of u and the clipped SSP fluxes r*_ij into r_up (after the rate pass)
+int mc_ssp_fluxes(afc_problem_s* p, const double* u);
 int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot,
                         bool want_F = false);
 

@@ -420,15 +420,29 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   if (stt) std::memset(stt, 0, sizeof(*stt));
   const int64_t N = p->N;
   const int lim = o->limiter;
-  if (lim != AFC_LIM_NONE && lim != AFC_LIM_GALERKIN && lim != AFC_LIM_ZALESAK) {
-    set_error("afc_step supports limiters NONE, GALERKIN, ZALESAK");
+  const bool ssp = o->scheme == AFC_SSP2 || o->scheme == AFC_SSP3;
+  if (lim == AFC_LIM_MC && ssp) {
+    // transient MC (Sec. 2.2): the SSP schemes with the MC limiter, FP64
+    if (p->family != AFC_FAMILY_MC) { set_error("transient MC needs the MC family assembly"); return AFC_E_STATE; }
+    if (o->precision != AFC_FP64) { set_error("transient MC runs in FP64 only"); return AFC_E_INVALID; }
+  } else if (lim != AFC_LIM_NONE && lim != AFC_LIM_GALERKIN && lim != AFC_LIM_ZALESAK) {
+    set_error("afc_step supports limiters NONE, GALERKIN, ZALESAK (and MC with the SSP schemes)");
     return AFC_E_INVALID;
   }
   cudaStream_t s = p->stream;
   const bool mixed = o->precision == AFC_MIXED;
   const bool graph = o->graph != 0;   // captured on a private stream, launched on the problem's stream
   if (graph && (o->scheme == AFC_SSP2 || o->scheme == AFC_SSP3)) return ssp_step_graph(p, o, stt);
-  if (graph && o->scheme == AFC_CN_NONLINEAR) {
+  // linear Zal+CN: one undamped correction from 2 u~ - u_old solves its linear system
+  afc_opts olin;
+  if (o->scheme == AFC_CN_LINEAR) {
+    olin = *o;
+    olin.fp_fixed_its = 1;
+    olin.omega = 1.0;
+    o = &olin;
+  }
+  const bool cn = o->scheme == AFC_CN_NONLINEAR || o->scheme == AFC_CN_LINEAR;
+  if (graph && cn) {
     if (p->family != AFC_FAMILY_FCT) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
     if ((st = build_cn_system(p, o->dt))) return st;
     return cn_step_graph(p, o, stt);
@@ -447,12 +461,16 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
     if (stt) stt->stages = 3;
     return finish_stats(p, stt, AFC_OK);
   }
-  if (o->scheme != AFC_CN_NONLINEAR) { set_error("unknown scheme"); return AFC_E_INVALID; }
+  if (!cn) { set_error("unknown scheme"); return AFC_E_INVALID; }
   if (p->family != AFC_FAMILY_FCT) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
   if ((st = build_cn_system(p, o->dt))) return st;
   if ((st = cn_predictor(p, p->u0.p, o->dt))) return st;
-  AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(N), kBlock, 0, s>>>(N, p->dir.p, p->udir.p, p->u.p));
-  AFC_CUDA(cudaGetLastError());
+  if (o->scheme == AFC_CN_LINEAR) {
+    if ((st = cn_linear_guess(p, p->u0.p, p->u.p))) return st;
+  } else {
+    AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(N), kBlock, 0, s>>>(N, p->dir.p, p->udir.p, p->u.p));
+    AFC_CUDA(cudaGetLastError());
+  }
   if ((st = cn_update(p, 0.0, nullptr, p->u.p, p->u0.p))) return st;
   const double dt = o->dt;
   st = fixed_point(
@@ -468,8 +486,8 @@ int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
   if (!o) { set_error("null options"); return AFC_E_INVALID; }
   if (stt) std::memset(stt, 0, sizeof(*stt));
   const int lim = o->limiter;
-  if (lim != AFC_LIM_NONE && lim != AFC_LIM_GALERKIN && lim != AFC_LIM_MC) {
-    set_error("afc_solve_stationary supports limiters NONE, GALERKIN, MC");
+  if (lim != AFC_LIM_NONE && lim != AFC_LIM_GALERKIN && lim != AFC_LIM_MC && lim != AFC_LIM_MU) {
+    set_error("afc_solve_stationary supports limiters NONE, GALERKIN, MC, MU");
     return AFC_E_INVALID;
   }
   if (lim != AFC_LIM_NONE && p->family != AFC_FAMILY_MC) {
@@ -520,6 +538,10 @@ int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax
   if (st) return st;
   if (!u) { set_error("null argument"); return AFC_E_INVALID; }
   if ((st = to_device(p, p->ustage.p, u, p->N))) return st;
+  if (limiter != AFC_LIM_NONE && limiter != AFC_LIM_GALERKIN && limiter != AFC_LIM_MC && limiter != AFC_LIM_MU) {
+    set_error("limiter must be NONE, GALERKIN, MC or MU");
+    return AFC_E_INVALID;
+  }
   if (p->family != AFC_FAMILY_MC && limiter != AFC_LIM_NONE) {
     set_error("the MC limiter and its Galerkin mode need afc_assemble(..., AFC_FAMILY_MC, ...)");
     return AFC_E_STATE;
@@ -534,8 +556,8 @@ int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax
 int afc_mc_residual_sweep(afc_problem p, int limiter) {
   int st = check(p, true);
   if (st) return st;
-  if (limiter != AFC_LIM_NONE && limiter != AFC_LIM_GALERKIN && limiter != AFC_LIM_MC) {
-    set_error("limiter must be NONE, GALERKIN or MC");
+  if (limiter != AFC_LIM_NONE && limiter != AFC_LIM_GALERKIN && limiter != AFC_LIM_MC && limiter != AFC_LIM_MU) {
+    set_error("limiter must be NONE, GALERKIN, MC or MU");
     return AFC_E_INVALID;
   }
   if (p->family != AFC_FAMILY_MC && limiter != AFC_LIM_NONE) { set_error("needs the MC family"); return AFC_E_STATE; }

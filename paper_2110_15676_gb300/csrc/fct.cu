@@ -247,6 +247,20 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
     if (st) return st;
   }
   const SspArrays arr = ssp_arrays(p);
+  if (limiter == AFC_LIM_MC) {
+    // transient MC (Sec. 2.2): rate, clipped fluxes, then the unweighted sum of r*
+    int st = AFC_OK;
+    with_K(p->K, [&](auto kc) {
+      constexpr int KT = decltype(kc)::value;
+      AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT, false><<<g, kBlock, 0, s>>>(p->offs, arr, uin, dt));
+      if ((st = mc_ssp_fluxes(p, uin))) return;
+      AFC_LAUNCH(p, "k_ssp_correct", k_ssp_correct<KT, false><<<g, kBlock, 0, s>>>(p->offs, arr, AFC_LIM_GALERKIN, dt,
+                                                                                  a, uA, b, out));
+    });
+    if (st) return st;
+    AFC_CUDA(cudaGetLastError());
+    return AFC_OK;
+  }
   auto run = [&](auto kc, auto mc) {
     constexpr int KT = decltype(kc)::value;
     constexpr bool MX = decltype(mc)::value;
@@ -262,6 +276,23 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
     if (mixed) run(kc, std::true_type{});
     else run(kc, std::false_type{});
   });
+  AFC_CUDA(cudaGetLastError());
+  return AFC_OK;
+}
+
+namespace {
+// linear Zal+CN: u = 2 u~ - u_old (the value u^n is replaced by in Eq. flux_002), u_D on Dirichlet rows
+__global__ void k_cn_linear_guess(int64_t N, const uint8_t* __restrict__ dir, const double* __restrict__ udir,
+                                  const double* __restrict__ ut, const double* __restrict__ u_old,
+                                  double* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) u[i] = dir[i] ? udir[i] : 2.0 * ut[i] - u_old[i];
+}
+}  // namespace
+
+int cn_linear_guess(afc_problem_s* p, const double* u_old, double* u) {
+  AFC_LAUNCH(p, "k_cn_linear_guess", k_cn_linear_guess<<<grid_for(p->N), kBlock, 0, p->stream>>>(
+                                         p->N, p->dir.p, p->udir.p, p->ut.p, u_old, u));
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }

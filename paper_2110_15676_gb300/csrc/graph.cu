@@ -316,8 +316,12 @@ int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
           AFC_LAUNCH(p, "k_copy", k_copy<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->u.p, p->u0.p));
           int s = cn_predictor(p, p->u0.p, dt);
           if (s) return s;
-          AFC_LAUNCH(p, "k_apply_dirichlet",
-                     k_apply_dirichlet_g<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->dir.p, p->udir.p, p->u.p));
+          if (o->scheme == AFC_CN_LINEAR) {
+            if ((s = cn_linear_guess(p, p->u0.p, p->u.p))) return s;
+          } else {
+            AFC_LAUNCH(p, "k_apply_dirichlet",
+                       k_apply_dirichlet_g<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->dir.p, p->udir.p, p->u.p));
+          }
           return cn_update(p, 0.0, nullptr, p->u.p, p->u0.p);
         },
         [&]() -> int { return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, p->scal.p); },

@@ -176,7 +176,180 @@ __global__ void k_mc_residual(int64_t N, Offsets of, int limiter, const unsigned
   block_sum_to(r2, part);
 }
 
+// ---- monolithic upwind (MU) limiter (Sec. 3, MU limiter) ------------------------
+// Stationary fluxes r_ij = d_ij (u_j - u_i), convective a_ij = k_ij (Remark
+// rem:assembling_mc).  The pair (i, j) belongs to i if a_ji < a_ij, and on a tie
+// a_ij = a_ji to the smaller index; its owner's factor is its alpha on both sides.
+// a_ij, a_ji are computed values: they tie when within 1e-12 (|a_ij| + |a_ji|), so an
+// exact tie of the exact entries does not depend on rounding.
+
+// a_ij and a_ji of the pair (i, i + o_k) as seen from row i
+__device__ __forceinline__ void pair_conv(const Offsets& of, int k, int64_t i, int64_t N,
+                                          const double* __restrict__ kij, const double* __restrict__ kji,
+                                          double& aij, double& aji) {
+  if (k > of.Kup) {
+    const int64_t q = (int64_t)(k - of.Kup - 1) * N + i;
+    aij = kij[q];
+    aji = kji[q];
+  } else {
+    const int64_t q = (int64_t)(of.Kup - 1 - k) * N + i + of.o[k];   // stored at the lower row j
+    aij = kji[q];
+    aji = kij[q];
+  }
+}
+
+__device__ __forceinline__ bool mu_owns(double aij, double aji, int k, int Kup) {
+  if (fabs(aij - aji) <= 1e-12 * (fabs(aij) + fabs(aji))) return k > Kup;   // tie: the smaller index (k > Kup: j > i)
+  return aji < aij;
+}
+
+// steps 1-3: P+/- over the owned pairs, Q+/- over all pairs, R+/-
+template <int KT>
+__global__ void k_mu_factors(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
+                             const double* __restrict__ d_up, const double* __restrict__ kij,
+                             const double* __restrict__ kji, const double* __restrict__ u,
+                             const uint8_t* __restrict__ dir, double* __restrict__ Rp, double* __restrict__ Rm) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (dir[i]) {
+    Rp[i] = 1.0;
+    Rm[i] = 1.0;
+    return;
+  }
+  const unsigned long long mk = mask[i];
+  const double ui = u[i];
+  double Pp = 0.0, Pm = 0.0, Qp = 0.0, Qm = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (k == Kup || !((mk >> k) & 1ull)) continue;
+    const double r = pair_d(of, k, i, N, d_up) * (u[i + of.o[k]] - ui);
+    double aij, aji;
+    pair_conv(of, k, i, N, kij, kji, aij, aji);
+    const bool own = mu_owns(aij, aji, k, Kup);
+    if (gt0(r)) {
+      Qm -= r;
+      if (own) Pp += r;
+    } else if (!is0(r)) {
+      Qp -= r;
+      if (own) Pm += r;
+    }
+  }
+  Rp[i] = zalesak_factor(Qp, Pp);
+  Rm[i] = zalesak_factor(Qm, Pm);
+}
+
+// step 4 and the residual res = f + F* - AA u (0 on Dirichlet rows), block partials
+// of res^2; F*_i = sum_j alpha_ij r_ij with the owner's factor
+template <int KT>
+__global__ void __launch_bounds__(256, 3) k_mu_residual(
+    int64_t N, Offsets of, const unsigned long long* __restrict__ mask, const double* __restrict__ d_up,
+    const double* __restrict__ kij, const double* __restrict__ kji, const double* __restrict__ AA,
+    const double* __restrict__ u, const double* __restrict__ f, const uint8_t* __restrict__ dir,
+    const double* __restrict__ Rp, const double* __restrict__ Rm, double* __restrict__ res,
+    double* __restrict__ Fout, double* __restrict__ part) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (i < N) {
+    double rv = 0.0, F = 0.0;
+    if (!dir[i]) {
+      const unsigned long long mk = mask[i];
+      const double ui = u[i], rpi = Rp[i], rmi = Rm[i];
+      double y = f[i];
+#pragma unroll
+      for (int k = 0; k < K; ++k) y = fma(-AA[k * N + i], u[i + of.o[k]], y);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (k == Kup || !((mk >> k) & 1ull)) continue;
+        const int64_t j = i + of.o[k];
+        const double r = pair_d(of, k, i, N, d_up) * (u[j] - ui);
+        if (is0(r)) continue;                         // alpha = 1, r = 0
+        double aij, aji;
+        pair_conv(of, k, i, N, kij, kji, aij, aji);
+        double alpha;
+        if (mu_owns(aij, aji, k, Kup)) alpha = gt0(r) ? rpi : rmi;
+        else alpha = gt0(r) ? Rm[j] : Rp[j];          // r_ji = -r_ij
+        F = fma(alpha, r, F);
+      }
+      rv = y + F;
+    }
+    res[i] = rv;
+    if (Fout) Fout[i] = F;
+    r2 = rv * rv;
+  }
+  block_sum_to(r2, part);
+}
+
+// ---- transient MC (Sec. 2.2): the SSP fluxes clipped by Eq. MClimiter ---------------
+template <int KT>
+__global__ void k_mcssp_bounds(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
+                               const double* __restrict__ u, double* __restrict__ umax, double* __restrict__ umin) {
+  const int K = KT > 0 ? KT : of.K;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const unsigned long long mk = mask[i];
+  long long kmax = dkey(u[i]), kmin = kmax;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!((mk >> k) & 1ull)) continue;
+    const long long kj = dkey(u[i + of.o[k]]);
+    kmax = kj > kmax ? kj : kmax;
+    kmin = kj < kmin ? kj : kmin;
+  }
+  umax[i] = from_key(kmax);
+  umin[i] = from_key(kmin);
+}
+
+// r*_ij of every pair i < j at row i: r_ij = m_ij (udot_i - udot_j) + d_ij (u_j - u_i)
+// (Eq. defn_r_ij_SSP) clipped with the bar states 2 d ubar_ij = d (u_i + u_j) + a_ij (u_j - u_i)
+// and the bounds of the stage input; r* = 0 where d_ij = 0 (A16)
+template <int KT>
+__global__ void k_mcssp_edges(int64_t N, Offsets of, const double* __restrict__ m_up, const double* __restrict__ d_up,
+                              const double* __restrict__ kij, const double* __restrict__ kji,
+                              const double* __restrict__ u, const double* __restrict__ udot,
+                              const double* __restrict__ umax, const double* __restrict__ umin,
+                              double* __restrict__ r_up) {
+  const int Kup = (KT > 0 ? KT : of.K) / 2;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double ui = u[i], udi = udot[i], mxi = umax[i], mni = umin[i];
+#pragma unroll
+  for (int ku = 0; ku < Kup; ++ku) {
+    const int64_t q = (int64_t)ku * N + i;
+    const int64_t j = i + of.o[Kup + 1 + ku];
+    const double d = d_up[q];
+    double rs = 0.0;
+    if (!is0(d)) {
+      const double uj = u[j];
+      const double r = fma(m_up[q], udi - udot[j], d * (uj - ui));
+      const double d2 = 2.0 * d;
+      const double ubij = (d * (ui + uj) + kij[q] * (uj - ui)) / d2;
+      const double ubji = (d * (uj + ui) + kji[q] * (ui - uj)) / d2;
+      if (gt0(r)) rs = imin(r, imin(d2 * (ubij - mxi), d2 * (umin[j] - ubji)));
+      else rs = imax(r, imax(d2 * (ubij - mni), d2 * (umax[j] - ubji)));
+    }
+    r_up[q] = rs;
+  }
+}
+
 }  // namespace
+
+int mc_ssp_fluxes(afc_problem_s* p, const double* u) {
+  const int64_t N = p->N;
+  const int64_t g = grid_for(N);
+  cudaStream_t s = p->stream;
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    AFC_LAUNCH(p, "k_mcssp_bounds",
+               k_mcssp_bounds<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, u, p->umax.p, p->umin.p));
+    AFC_LAUNCH(p, "k_mcssp_edges",
+               k_mcssp_edges<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->m_up.p, p->d_up.p, p->kij_up.p, p->kji_up.p, u,
+                                                      p->udot.p, p->umax.p, p->umin.p, p->r_up.p));
+  });
+  AFC_CUDA(cudaGetLastError());
+  return AFC_OK;
+}
 
 int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot,
                         bool want_F) {
@@ -186,6 +359,16 @@ int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* 
   const double* Mop = limiter == AFC_LIM_NONE ? p->AA.p : p->AG.p;
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
+    if (limiter == AFC_LIM_MU) {
+      AFC_LAUNCH(p, "k_mu_factors",
+                 k_mu_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->d_up.p, p->kij_up.p, p->kji_up.p,
+                                                       u, p->dir.p, p->Rp.p, p->Rm.p));
+      AFC_LAUNCH(p, "k_mu_residual",
+                 k_mu_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->d_up.p, p->kij_up.p, p->kji_up.p,
+                                                        p->AA.p, u, p->f.p, p->dir.p, p->Rp.p, p->Rm.p, res,
+                                                        want_F ? p->Fs.p : nullptr, p->part.p));
+      return;
+    }
     if (limiter == AFC_LIM_MC) {
       AFC_LAUNCH(p, "k_mc_bounds",
                  k_mc_bounds<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, u, want_F ? p->umax.p : nullptr,

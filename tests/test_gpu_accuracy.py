@@ -1,5 +1,5 @@
 """The CUDA path on the paper's circular convection example (MC limiter, stationary,
-Kuhn P1 levels 5 and 6): errors equal the oracle's at level 5, are of the printed
+Kuhn P1 levels 5 and 6; MC, and MU at level 5): errors equal the oracle's at level 5, are of the printed
 order at both levels, and decrease with refinement."""
 import os
 
@@ -14,7 +14,7 @@ from test_oracle_accuracy import printed_errors, stored_oracle
 pytestmark = pytest.mark.gpu
 
 
-def gpu_errors(level, precision):
+def gpu_errors(level, precision, limiter="mc"):
     from paper_2110_15676_gb300 import afc
     n = 2 ** level + 1
     wl = W.circular_convection(n)
@@ -22,7 +22,8 @@ def gpu_errors(level, precision):
                     precision=precision)
     g.set_solution(wl.u0)
     mixed = precision == "mixed"
-    opts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
+    lim = afc.AFC_LIM_MC if limiter == "mc" else afc.AFC_LIM_MU
+    opts = afc.default_opts(limiter=lim, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
                             ksp_rtol=1e-6 if mixed else 1e-10, fp_tol=1e-13, fp_maxit=6000,
                             precision=afc.AFC_MIXED if mixed else afc.AFC_FP64)
     st = g.solve_stationary(opts)
@@ -33,11 +34,11 @@ def gpu_errors(level, precision):
     return st, u, e1, e2
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_circular_convection_level5_equals_oracle(precision):
-    st, u, e1, e2 = gpu_errors(5, precision)
+@pytest.mark.parametrize("precision,limiter", [("fp64", "mc"), ("mixed", "mc"), ("mixed", "mu")])
+def test_circular_convection_level5_equals_oracle(precision, limiter):
+    st, u, e1, e2 = gpu_errors(5, precision, limiter)
     assert st["status"] == 0, st
-    s1, s2 = stored_oracle()[5]
+    s1, s2 = stored_oracle(limiter)[5]
     assert abs(e1 - s1) < 1e-6 * s1 and abs(e2 - s2) < 1e-6 * s2, (e1, e2, s1, s2)
     assert u.min() >= -1e-14 and u.max() <= 1.0 + 1e-14
 

@@ -204,6 +204,69 @@ def test_cn_steps_parity(afc, elem, n, precision, graph):
         assert st["outer_its"] == 6
 
 
+@pytest.mark.parametrize("elem,n", [("q1", 9), ("p1", 8)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_cn_linear_steps_parity(afc, elem, n, precision, graph):
+    """Linear Zal+CN: 4 steps against the oracle's literal linear scheme (direct solve)."""
+    wl = W.rotating_transient(elem, n)
+    o, g = pair_from_workload(wl, precision=precision)
+    dt = O.cfl_timestep(o, 1.0)
+    u = wl.u0.copy()
+    g.set_solution(u)
+    mixed = precision == "mixed"
+    opts = afc.default_opts(scheme=afc.AFC_CN_LINEAR, dt=dt, ksp_atol=0.0 if mixed else 1e-14,
+                            ksp_rtol=1e-7 if mixed else 0.0,
+                            precision=afc.AFC_MIXED if mixed else afc.AFC_FP64, graph=graph)
+    for step in range(4):
+        u, _ = O.cn_linear_step(o, u, dt)
+        st = g.step(opts)
+        ug = g.get_solution()
+        assert relerr(ug, u) < (1e-6 if mixed else STEP_TOL), step
+        assert st["outer_its"] == 1
+
+
+@pytest.mark.parametrize("elem,n", [("p1", 9), ("q1", 8)])
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_transient_mc_steps_parity(afc, elem, n, order, graph):
+    """SSP2/SSP3 with the MC limiter (MC family), CFL 0.5, 10 steps."""
+    wl = W.rotating_transient(elem, n)
+    o, g = pair_from_workload(wl, "mc")
+    dt = O.cfl_timestep(o, 0.5)
+    u = wl.u0.copy()
+    g.set_solution(u)
+    opts = afc.default_opts(scheme=afc.AFC_SSP2 if order == 2 else afc.AFC_SSP3, limiter=afc.AFC_LIM_MC, dt=dt,
+                            graph=graph)
+    for step in range(10):
+        u = O.ssp_step(o, u, dt, order=order, mode="mc")
+        g.step(opts)
+        ug = g.get_solution()
+        assert relerr(ug, u) < STEP_TOL, step
+        assert ug.min() >= -1e-14 and ug.max() <= 1 + 1e-14
+
+
+def test_transient_mc_stage_parity_and_errors(afc):
+    wl = random_workload("q1", (7, 8, 6), seed=44)
+    o, g = pair_from_workload(wl, "mc")
+    dt = O.cfl_timestep(o, 0.5)
+    g.set_solution(wl.u0)
+    out = g.fe_stage(dt, afc.AFC_LIM_MC)
+    un, info = O.fe_mc_stage(o, wl.u0, dt, want=True)
+    free = ~o.dir_mask
+    Fs = max(np.abs(info["Fstar"]).max(), 1e-300)
+    assert np.abs(out["Fstar"] - info["Fstar"])[free].max() <= PASS_TOL * Fs * 10
+    assert relerr(out["u_new"], un) < PASS_TOL * 10
+    # transient MC needs the MC family and runs in FP64
+    gf = gpu_problem(wl.elem, wl.n, wl.b, wl.eps, wl.c, wl.f, wl.dir_mask, wl.u_dir)
+    with pytest.raises(afc.AfcError) as e:
+        gf.step(afc.default_opts(scheme=afc.AFC_SSP3, limiter=afc.AFC_LIM_MC, dt=dt))
+    assert e.value.status == afc.AFC_E_STATE
+    with pytest.raises(afc.AfcError) as e:
+        g.step(afc.default_opts(scheme=afc.AFC_SSP3, limiter=afc.AFC_LIM_MC, dt=dt, precision=afc.AFC_MIXED))
+    assert e.value.status == afc.AFC_E_INVALID
+
+
 def test_cn_converged_step_matches_oracle_tolerance(afc):
     wl = W.rotating_transient("q1", 11)
     o, g = pair_from_workload(wl)
@@ -234,6 +297,33 @@ def test_mc_limited_sum_parity(afc, elem, n, limiter):
     assert np.abs(out["Fstar"] - F)[free].max() <= PASS_TOL * Fs * 10
     if limiter == "mc":
         assert np.array_equal(out["umax"], d["umax"]) and np.array_equal(out["umin"], d["umin"])
+
+
+@pytest.mark.parametrize("elem,n", [("p1", 9), ("q1", (8, 7, 6))])
+def test_mu_limited_sum_parity(afc, elem, n):
+    wl = random_workload(elem, n, seed=22)
+    o, g = pair_from_workload(wl, "mc")
+    rng = np.random.default_rng(5)
+    u = rng.uniform(0, 1, o.mesh.n_nodes)
+    rstar, _ = O.mu_limited_fluxes(o, u)
+    F = O.limited_sum(o, np.ones_like(rstar), rstar)
+    out = g.mc_limited_sum(u, afc.AFC_LIM_MU)
+    free = ~o.dir_mask
+    assert np.abs(out["Fstar"] - F)[free].max() <= PASS_TOL * max(np.abs(F).max(), 1e-300) * 10
+
+
+@pytest.mark.parametrize("elem", ["p1", "q1"])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_mu_stationary_parity(afc, elem, graph):
+    wl = W.stationary_inflow(elem, 9)
+    o, g = pair_from_workload(wl, "mc")
+    u_ref, st_o = O.mc_stationary(o, tol=1e-12, omega=0.5, mode="mu", ksp="direct", max_outer=3000)
+    assert st_o["converged"]
+    g.set_solution(wl.u0)
+    st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MU, fp_tol=1e-12, omega=0.5, ksp=afc.AFC_KSP_GMRES,
+                                             ksp_atol=1e-14, fp_maxit=3000, graph=graph))
+    assert st["status"] == afc.AFC_OK
+    assert relerr(g.get_solution(), u_ref) < STEP_TOL
 
 
 @pytest.mark.parametrize("elem", ["p1", "q1"])

@@ -1,5 +1,5 @@
 """Paper-scale accuracy pin of the whole discretisation: the circular convection
-example with the MC limiter.  The oracle's L1 / L2 errors at refinement level 5
+example with the MC and MU limiters.  The oracle's L1 / L2 errors at refinement level 5
 (33 nodes per side) must be of the order the paper prints (within 30 %, the loose
 pin: the paper's tetrahedra come from red refinement, these from the Kuhn split of
 the same nodes), and the quadrature behind the error norms is pinned first."""
@@ -15,25 +15,29 @@ from paper_2110_15676_gb300 import workloads as W
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def printed_errors():
+def printed_errors(limiter="mc"):
+    """{level: (nodes per side, L1, L2)} of the paper's table for MC or MU."""
+    col = {"mc": 2, "mu": 4}[limiter]
     out = {}
     with open(os.path.join(GOLDEN, "circular_convection_errors.txt")) as fh:
         for line in fh:
             if line.startswith("#") or not line.strip():
                 continue
-            lv, n, l1, l2 = line.split()
-            out[int(lv)] = (int(n), float(l1), float(l2))
+            f = line.split()
+            out[int(f[0])] = (int(f[1]), float(f[col]), float(f[col + 1]))
     return out
 
 
-def stored_oracle():
+def stored_oracle(limiter="mc"):
+    """{level: (L1, L2)} written by tests/golden/make_circular_oracle.py."""
     out = {}
     with open(os.path.join(GOLDEN, "circular_convection_oracle.txt")) as fh:
         for line in fh:
             if line.startswith("#") or not line.strip():
                 continue
             f = line.split()
-            out[int(f[0])] = (float(f[4]), float(f[5]))
+            if f[2] == limiter:
+                out[int(f[0])] = (float(f[5]), float(f[6]))
     return out
 
 
@@ -57,13 +61,14 @@ def test_error_norms_closed_forms():
     assert abs(e1 - 0.25) < 1e-14 and abs(e2 - 1.0 / 3.0) < 1e-14
 
 
-def test_circular_convection_mc_errors_match_the_printed_order():
-    ref = printed_errors()
+@pytest.mark.parametrize("limiter", ["mc", "mu"])
+def test_circular_convection_errors_match_the_printed_order(limiter):
+    ref = printed_errors(limiter)
     n, p1, p2 = ref[5]
     wl = W.circular_convection(n)
     mesh = O.structured_mesh("p1", n)
     prob = O.assemble(mesh, wl.eps, wl.b, wl.c, wl.f, wl.dir_mask.astype(bool), wl.u_dir, "mc")
-    u, st = O.mc_stationary(prob, wl.u0, tol=1e-9, max_outer=5000, omega=0.5, mode="mc", ksp="direct")
+    u, st = O.mc_stationary(prob, wl.u0, tol=1e-9, max_outer=5000, omega=0.5, mode=limiter, ksp="direct")
     assert st["converged"]
     exact = lambda X, Y, Z: W.circular_exact(X, Y)  # noqa: E731
     e1, e2 = O.p1_error_norms(mesh, u, exact)
@@ -76,5 +81,5 @@ def test_circular_convection_mc_errors_match_the_printed_order():
     l1, l2 = O.p1_error_norms(mesh, ul, exact)
     assert e1 < 0.5 * l1 and e2 < 0.7 * l2
     # the stored oracle values (converged further) agree
-    s1, s2 = stored_oracle()[5]
+    s1, s2 = stored_oracle(limiter)[5]
     assert abs(e1 - s1) < 1e-5 * s1 and abs(e2 - s2) < 1e-5 * s2
