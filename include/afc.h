@@ -179,6 +179,9 @@ void afc_default_opts(afc_opts* o);
  *    With limiter AFC_LIM_MC (MC family, FP64) each stage is the transient MC
  *    update of Sec. 2.2: the fluxes Eq. defn_r_ij_SSP clipped by Eq. MClimiter
  *    with the bounds and bar states of the stage input.
+ *    With AFC_LIM_MC (MC family) the CN step uses F* = (F*(u^n) + F*(u^{n-1})) / 2
+ *    with F*(u) = sum_j r*_ij(u), the fluxes of Eq. defn_r_ij_SSP clipped by
+ *    Eq. MClimiter (Sec. 2.2).
  *  AFC_CN_LINEAR: linear Zal+CN (Sec. 2.1.1): u^n in Eq. flux_002 is replaced by
  *    2 u~ - u^{n-1}, so F* is known before the step and Eq. CNZal is one linear
  *    system, solved by one Krylov solve (fp_tol, fp_maxit, omega are not used).

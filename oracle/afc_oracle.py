@@ -407,6 +407,52 @@ def cn_system_matrix(prob: Problem, dt):
     return B.tocsr()
 
 
+def mc_transient_flux_sum(prob: Problem, u):
+    """F*_i(u) = sum_j r*_ij(u) of the transient MC scheme (Sec. 2.2): fluxes
+    Eq. defn_r_ij_SSP with the low-order rate at u, clipped by Eq. MClimiter."""
+    udot = low_order_rate(prob, u)
+    rstar, _ = mc_clip(prob, u, ssp_fluxes(prob, u, udot))
+    return limited_sum(prob, np.ones_like(rstar), rstar)
+
+
+def cn_mc_step(prob: Problem, u_old, dt, tol=1e-10, max_outer=100, omega=1.0, ksp="direct", ksp_atol=1e-12,
+               ksp_rtol=0.0, ksp_maxit=1000, gmres_restart=20, fixed_iterations=None):
+    """One CN step with the MC limiter (Sec. 2.2): Eq. CNZal with
+    F* = (F*(u^n) + F*(u^{n-1})) / 2, F*(u) = sum_j r*_ij(u) (mc_transient_flux_sum),
+    by the damped fixed point of Sec. 4 from u^{n-1}; MC family.  Returns (u_new, stats)."""
+    N = prob.mesh.n_nodes
+    dirm = prob.dir_mask
+    b0 = prob.mL / dt * u_old - 0.5 * (prob.AA @ u_old) + prob.f
+    F_old = mc_transient_flux_sum(prob, u_old)
+    Bsys = cn_system_matrix(prob, dt)
+    dinv = 1.0 / Bsys.diagonal()
+    lu = spla.splu(Bsys.tocsc()) if ksp == "direct" else None
+    u = u_old.copy()
+    u[dirm] = prob.u_dir[dirm]
+    stats = dict(outer_its=0, inner_its=0, res_hist=[])
+    for it in range(max_outer + 1):
+        Fstar = 0.5 * (mc_transient_flux_sum(prob, u) + F_old)
+        res = b0 + Fstar - (prob.mL / dt * u + 0.5 * (prob.AA @ u))
+        res[dirm] = 0.0
+        R = float(np.linalg.norm(res))
+        stats["res_hist"].append(R)
+        if fixed_iterations is None:
+            if R < math.sqrt(N) * tol or it == max_outer:
+                break
+        elif it == fixed_iterations:
+            break
+        if lu is not None:
+            delta = lu.solve(res)
+        else:
+            delta, kst = krylov_solve(Bsys, res, dinv, ksp, ksp_atol, ksp_rtol, ksp_maxit, gmres_restart)
+            stats["inner_its"] += kst["its"]
+        u = u + omega * delta
+        stats["outer_its"] += 1
+    stats["res_final"] = stats["res_hist"][-1]
+    stats["converged"] = stats["res_final"] < math.sqrt(N) * tol
+    return u, stats
+
+
 def cn_linear_step(prob: Problem, u_old, dt, prelimit=True, mode="zalesak", ksp="direct", ksp_atol=1e-12,
                    ksp_rtol=0.0, ksp_maxit=1000, gmres_restart=20):
     """One step of linear Zal+CN (Sec. 2.1.1, the linearised scheme): u^n in the flux

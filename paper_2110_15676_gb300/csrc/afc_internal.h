@@ -147,6 +147,7 @@ struct afc_problem_s {
   // state and work vectors (node vectors carry the halo)
   afc::DBuf<double> u, u0, ustage, udot, ut, Rp, Rm, Fs, Qp, Qm, b0, res, delta, umax, umin, tmp, cn_a, cn_s;
   afc::DBuf<double> bA, bB;         // MC: u_max - u and u - u_min
+  afc::DBuf<double> Fold;           // CN with the MC limiter: F*(u^{n-1})
   afc::DBuf<unsigned int> clip;     // MC: per row, bit ku set if the pair (i, i + o) was clipped
   afc::DBuf<float4> nodef;          // MC: (u, u_max - u, u - u_min) rounded to single
   afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
@@ -182,6 +183,9 @@ SspArrays ssp_arrays(afc_problem_s* p);
 // CN helpers
 int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
 int cn_linear_guess(afc_problem_s* p, const double* u_old, double* u);             // u = 2 ut - u_old (after cn_predictor)
+// CN with the MC limiter (Sec. 2.2): Fold = F*(u_old), then res = b0 + (F*(u) + Fold)/2 - (M_L/dt + AA/2) u
+int mc_cn_old_flux(afc_problem_s* p, const double* u_old);
+int mc_cn_residual(afc_problem_s* p, const double* u, double* res, double* normsq_slot);
 // a = u - u_old, s = u + u_old after u += omega * delta (delta may be null)
 int cn_update(afc_problem_s* p, double omega, const double* delta, double* u, const double* u_old);
 int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int limiter, int prelimit, double* res,

@@ -81,7 +81,7 @@ int create_common(afc_problem_s* p) {
     return st;
   DBuf<double>* vecs[] = {&p->u,  &p->u0,  &p->ustage, &p->udot, &p->ut,   &p->Rp,  &p->Rm,
                           &p->Fs, &p->Qp,  &p->Qm,     &p->b0,   &p->res,  &p->delta, &p->umax,
-                          &p->umin, &p->tmp, &p->cn_a, &p->cn_s, &p->bA, &p->bB};
+                          &p->umin, &p->tmp, &p->cn_a, &p->cn_s, &p->bA, &p->bB, &p->Fold};
   for (auto* v : vecs)
     if ((st = v->alloc(N, p->pad))) return st;
   if ((st = p->scal.alloc(64)) || (st = p->part.alloc(4 * std::max<int64_t>(kRedBlocks, grid_for(N))))) return st;
@@ -110,7 +110,7 @@ void destroy_all(afc_problem_s* p) {
                         &p->u, &p->u0, &p->ustage, &p->udot, &p->ut, &p->Rp, &p->Rm, &p->Fs, &p->Qp, &p->Qm,
                         &p->b0, &p->res, &p->delta, &p->umax, &p->umin, &p->tmp, &p->cn_a, &p->cn_s,
                         &p->scal, &p->part, &p->r_up, &p->mdt_up, &p->mLdt, &p->kij_up, &p->kji_up,
-                        &p->AG, &p->bA, &p->bB, &p->d2_up};
+                        &p->AG, &p->bA, &p->bB, &p->d2_up, &p->Fold};
   for (auto* b : dv) b->free_();
   p->Bst32.free_(); p->dinv_st32.free_(); p->Bcn32.free_(); p->dinv_cn32.free_();
   p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_(); p->clip.free_();
@@ -421,14 +421,15 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   const int64_t N = p->N;
   const int lim = o->limiter;
   const bool ssp = o->scheme == AFC_SSP2 || o->scheme == AFC_SSP3;
-  if (lim == AFC_LIM_MC && ssp) {
-    // transient MC (Sec. 2.2): the SSP schemes with the MC limiter, FP64
+  if (lim == AFC_LIM_MC && (ssp || o->scheme == AFC_CN_NONLINEAR)) {
+    // transient MC (Sec. 2.2): the SSP schemes (FP64) or nonlinear CN with the MC limiter
     if (p->family != AFC_FAMILY_MC) { set_error("transient MC needs the MC family assembly"); return AFC_E_STATE; }
-    if (o->precision != AFC_FP64) { set_error("transient MC runs in FP64 only"); return AFC_E_INVALID; }
+    if (ssp && o->precision != AFC_FP64) { set_error("transient MC with SSP runs in FP64 only"); return AFC_E_INVALID; }
   } else if (lim != AFC_LIM_NONE && lim != AFC_LIM_GALERKIN && lim != AFC_LIM_ZALESAK) {
-    set_error("afc_step supports limiters NONE, GALERKIN, ZALESAK (and MC with the SSP schemes)");
+    set_error("afc_step supports limiters NONE, GALERKIN, ZALESAK (and MC with SSP2, SSP3, CN_NONLINEAR)");
     return AFC_E_INVALID;
   }
+  const int cn_family = lim == AFC_LIM_MC ? AFC_FAMILY_MC : AFC_FAMILY_FCT;
   cudaStream_t s = p->stream;
   const bool mixed = o->precision == AFC_MIXED;
   const bool graph = o->graph != 0;   // captured on a private stream, launched on the problem's stream
@@ -443,7 +444,7 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   }
   const bool cn = o->scheme == AFC_CN_NONLINEAR || o->scheme == AFC_CN_LINEAR;
   if (graph && cn) {
-    if (p->family != AFC_FAMILY_FCT) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
+    if (p->family != cn_family) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
     if ((st = build_cn_system(p, o->dt))) return st;
     return cn_step_graph(p, o, stt);
   }
@@ -462,9 +463,20 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
     return finish_stats(p, stt, AFC_OK);
   }
   if (!cn) { set_error("unknown scheme"); return AFC_E_INVALID; }
-  if (p->family != AFC_FAMILY_FCT) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
+  if (p->family != cn_family) { set_error("CN FCT needs the FCT family"); return AFC_E_STATE; }
   if ((st = build_cn_system(p, o->dt))) return st;
   if ((st = cn_predictor(p, p->u0.p, o->dt))) return st;
+  if (lim == AFC_LIM_MC) {
+    // CN with the MC limiter: F* = (F*(u) + F*(u_old)) / 2, plain damped updates
+    AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(N), kBlock, 0, s>>>(N, p->dir.p, p->udir.p, p->u.p));
+    AFC_CUDA(cudaGetLastError());
+    if ((st = mc_cn_old_flux(p, p->u0.p))) return st;
+    st = fixed_point(
+        p, o, 1, stt, [&]() { return mc_cn_residual(p, p->u.p, p->res.p, p->scal.p); },
+        [&]() { return axpy_device(p, o->omega, p->delta.p, p->u.p); });
+    if (st < 0) return st;
+    return finish_stats(p, stt, st);
+  }
   if (o->scheme == AFC_CN_LINEAR) {
     if ((st = cn_linear_guess(p, p->u0.p, p->u.p))) return st;
   } else {

@@ -320,6 +320,97 @@ int cn_update(afc_problem_s* p, double omega, const double* delta, double* u, co
   return AFC_OK;
 }
 
+namespace {
+
+// F*_i = sum_j r*_ij of the clipped fluxes stored once per pair (0 on Dirichlet rows)
+template <int KT>
+__global__ void k_pair_sum(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
+                           const double* __restrict__ r_up, const uint8_t* __restrict__ dir, double* __restrict__ F) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s = 0.0;
+  if (!dir[i]) {
+    const unsigned long long mk = mask[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (k == Kup || !((mk >> k) & 1ull)) continue;
+      s += pair_flux(of, Kup, k, i, N, r_up);
+    }
+  }
+  F[i] = s;
+}
+
+// res = b0 + (F*(u) + Fold) / 2 - (m/dt u + AA u / 2) on free rows, block partials of res^2
+template <int KT>
+__global__ void __launch_bounds__(256, 3) k_mccn_residual(
+    int64_t N, Offsets of, const unsigned long long* __restrict__ mask, const double* __restrict__ r_up,
+    const double* __restrict__ AA, const double* __restrict__ u, const double* __restrict__ Fold,
+    const double* __restrict__ b0, const double* __restrict__ mLdt, const uint8_t* __restrict__ dir,
+    double* __restrict__ res, double* __restrict__ Fout, double* __restrict__ part) {
+  const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (i < N) {
+    double rv = 0.0, F = 0.0;
+    if (!dir[i]) {
+      const unsigned long long mk = mask[i];
+      double y = 0.0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], u[i + of.o[k]], y);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (k == Kup || !((mk >> k) & 1ull)) continue;
+        F += pair_flux(of, Kup, k, i, N, r_up);
+      }
+      F = 0.5 * (F + Fold[i]);
+      rv = b0[i] + F - (mLdt[i] * u[i] + 0.5 * y);
+    }
+    res[i] = rv;
+    if (Fout) Fout[i] = F;
+    r2 = rv * rv;
+  }
+  block_sum_to(r2, part);
+}
+
+}  // namespace
+
+int mc_cn_old_flux(afc_problem_s* p, const double* u_old) {
+  const int64_t N = p->N, g = grid_for(N);
+  cudaStream_t s = p->stream;
+  const SspArrays arr = ssp_arrays(p);
+  int st = AFC_OK;
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT, false><<<g, kBlock, 0, s>>>(p->offs, arr, u_old, 0.0));
+    if ((st = mc_ssp_fluxes(p, u_old))) return;
+    AFC_LAUNCH(p, "k_pair_sum", k_pair_sum<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->dir.p,
+                                                                      p->Fold.p));
+  });
+  if (st) return st;
+  AFC_CUDA(cudaGetLastError());
+  return AFC_OK;
+}
+
+int mc_cn_residual(afc_problem_s* p, const double* u, double* res, double* normsq_slot) {
+  const int64_t N = p->N, g = grid_for(N);
+  cudaStream_t s = p->stream;
+  const SspArrays arr = ssp_arrays(p);
+  int st = AFC_OK;
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    AFC_LAUNCH(p, "k_ssp_rate", k_ssp_rate<KT, false><<<g, kBlock, 0, s>>>(p->offs, arr, u, 0.0));
+    if ((st = mc_ssp_fluxes(p, u))) return;
+    AFC_LAUNCH(p, "k_mccn_residual",
+               k_mccn_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->AA.p, u, p->Fold.p,
+                                                        p->b0.p, p->mLdt.p, p->dir.p, res, p->Fs.p, p->part.p));
+  });
+  if (st) return st;
+  finalize_sum(p, p->part.p, (int)g, normsq_slot);
+  AFC_CUDA(cudaGetLastError());
+  return AFC_OK;
+}
+
 int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int limiter, int prelimit, double* res,
                         double* normsq_slot) {
   const int64_t N = p->N;

@@ -316,6 +316,11 @@ int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
           AFC_LAUNCH(p, "k_copy", k_copy<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->u.p, p->u0.p));
           int s = cn_predictor(p, p->u0.p, dt);
           if (s) return s;
+          if (lim == AFC_LIM_MC) {
+            AFC_LAUNCH(p, "k_apply_dirichlet",
+                       k_apply_dirichlet_g<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->dir.p, p->udir.p, p->u.p));
+            return mc_cn_old_flux(p, p->u0.p);
+          }
           if (o->scheme == AFC_CN_LINEAR) {
             if ((s = cn_linear_guess(p, p->u0.p, p->u.p))) return s;
           } else {
@@ -324,8 +329,14 @@ int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
           }
           return cn_update(p, 0.0, nullptr, p->u.p, p->u0.p);
         },
-        [&]() -> int { return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, p->scal.p); },
-        [&]() -> int { return cn_update(p, o->omega, p->delta.p, p->u.p, p->u0.p); }, *p->g_step);
+        [&]() -> int {
+          if (lim == AFC_LIM_MC) return mc_cn_residual(p, p->u.p, p->res.p, p->scal.p);
+          return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, p->scal.p);
+        },
+        [&]() -> int {
+          if (lim == AFC_LIM_MC) return axpy_device(p, o->omega, p->delta.p, p->u.p);
+          return cn_update(p, o->omega, p->delta.p, p->u.p, p->u0.p);
+        }, *p->g_step);
     if (st) {
       drop(p->g_step);
       return st;

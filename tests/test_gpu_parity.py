@@ -246,6 +246,27 @@ def test_transient_mc_steps_parity(afc, elem, n, order, graph):
         assert ug.min() >= -1e-14 and ug.max() <= 1 + 1e-14
 
 
+@pytest.mark.parametrize("elem,n", [("p1", 9), ("q1", 8)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_cn_mc_steps_parity(afc, elem, n, precision, graph):
+    """Nonlinear CN with the MC limiter, CFL 1, 3 steps of 6 fixed-point corrections."""
+    wl = W.rotating_transient(elem, n)
+    o, g = pair_from_workload(wl, "mc", precision=precision)
+    dt = O.cfl_timestep(o, 1.0)
+    u = wl.u0.copy()
+    g.set_solution(u)
+    mixed = precision == "mixed"
+    opts = afc.default_opts(scheme=afc.AFC_CN_NONLINEAR, limiter=afc.AFC_LIM_MC, dt=dt, fp_fixed_its=6,
+                            ksp_atol=0.0 if mixed else 1e-14, ksp_rtol=1e-7 if mixed else 0.0,
+                            precision=afc.AFC_MIXED if mixed else afc.AFC_FP64, graph=graph)
+    for step in range(3):
+        u, _ = O.cn_mc_step(o, u, dt, fixed_iterations=6)
+        st = g.step(opts)
+        assert relerr(g.get_solution(), u) < (1e-6 if mixed else STEP_TOL), step
+        assert st["outer_its"] == 6
+
+
 def test_transient_mc_stage_parity_and_errors(afc):
     wl = random_workload("q1", (7, 8, 6), seed=44)
     o, g = pair_from_workload(wl, "mc")

@@ -129,3 +129,24 @@ def test_transient_mc_preserves_constants():
                        family="mc")
     u = O.ssp_step(o, np.full(N, 0.3), O.cfl_timestep(o, 0.5), order=3, mode="mc")
     assert np.abs(u - 0.3).max() < 1e-15
+
+
+# ---- CN with the MC limiter (Sec. 2.2) -------------------------------------------
+def test_cn_mc_agrees_with_ssp_mc_for_small_steps_and_keeps_constants():
+    """CN and SSP3 both integrate the same semi-discrete MC scheme: for a small step
+    their updates agree to a small fraction of the step's change (second order in
+    dt), and a constant state stays constant."""
+    from paper_2110_15676_gb300 import workloads as Wk
+    wl = Wk.rotating_transient("p1", 9)
+    o = oracle_problem(wl.elem, wl.n, wl.b, wl.eps, wl.c, wl.f, wl.dir_mask, wl.u_dir, family="mc")
+    dt = O.cfl_timestep(o, 0.05)
+    uc, st = O.cn_mc_step(o, wl.u0, dt, tol=1e-13, max_outer=300)
+    assert st["converged"]
+    us = O.ssp_step(o, wl.u0, dt, order=3, mode="mc")
+    assert np.abs(uc - us).max() < 1e-3 * np.abs(us - wl.u0).max()
+    N = o.mesh.n_nodes
+    oc = oracle_problem("p1", 9, wl.b, wl.eps, 0.0, np.zeros(N), wl.dir_mask, np.full(N, 0.6), family="mc")
+    u1, _ = O.cn_mc_step(oc, np.full(N, 0.6), O.cfl_timestep(oc, 1.0), tol=1e-13, max_outer=50)
+    assert np.abs(u1 - 0.6).max() < 1e-13
+    # both flux halves are conservative
+    assert abs(O.mc_transient_flux_sum(o, uc).sum()) < 1e-14 * np.abs(uc).sum()
