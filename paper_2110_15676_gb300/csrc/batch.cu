@@ -32,6 +32,7 @@
 #include "afc_internal.h"
 #include "kernels_common.cuh"
 #include "ssp_rows.cuh"
+#include "grid_sync.cuh"
 
 namespace afc {
 namespace {
@@ -52,51 +53,6 @@ struct StageArgs {
   int in[3], uA[3], out[3];
   double ca[3], cb[3];
 };
-
-struct GridBar {
-  unsigned int count;   // blocks arrived at the current barrier
-  unsigned int gen;     // barrier generation
-  int err;              // 1 after a wait gave up
-  int pad;
-};
-
-constexpr unsigned long long kBarrierWaitNs = 4000000000ull;   // 4 s of the global timer
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier of a cooperative launch, with a bounded wait.
-__device__ void grid_barrier(GridBar* gb) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &gb->gen;
-    volatile int* verr = &gb->err;
-    const unsigned int g0 = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&gb->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);   // reset before the release
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else if (*verr == 0) {
-      const unsigned long long t0 = global_ns();
-      while (*vgen == g0) {
-        if (*verr != 0) break;
-        if (global_ns() - t0 > kBarrierWaitNs) {
-          atomicExch(&gb->err, 1);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
 
 template <int KT, bool MIXED>
 __device__ __forceinline__ void batch_row(const BInst& in, int phase, int st, const StageArgs& sa, int limiter,

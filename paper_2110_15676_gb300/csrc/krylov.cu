@@ -14,6 +14,7 @@
 #include "afc_internal.h"
 #include "graph_util.h"
 #include "kernels_common.cuh"
+#include "grid_sync.cuh"
 
 namespace afc {
 
@@ -201,6 +202,9 @@ struct KrylovWork {
   DBuf<char> vec;       // all vectors (with halos)
   DBuf<double> sc, part;
   DBuf<unsigned int> counter;
+  DBuf<unsigned int> barrier;   // GridBar of the persistent BiCGStab launch
+  int coop = -1;                // device supports cooperative launches (-1: not asked yet)
+  int nsm = 0;
   double* hsc = nullptr;
   size_t vstride = 0;   // elements per vector incl. halo
 };
@@ -436,6 +440,159 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
     else if (stop_test(nr, sc)) sc[S_DONE] = 1.0;
     else if (sc[S_ITS] >= sc[S_MAXIT]) sc[S_DONE] = 4.0;
     if (cond.use) cudaGraphSetConditional(cond.h, sc[S_DONE] == 0.0 ? 1u : 0u);
+  }
+}
+
+// ---- BiCGStab as one persistent cooperative launch ----------------------------
+// The five phases of an iteration (p update, v = B phat, s update, t = B shat, x / r
+// update) run in one launch, separated by grid barriers; nothing returns to the
+// host or the graph between iterations.  A grid-wide sum: every block stores its
+// partials, waits at the barrier, then sums all blocks' partials in block order.
+// The order is the same in every block, so every block obtains the same totals
+// bit for bit and takes the same branches.  Partials alternate between two buffers
+// (a block can run at most one reduction ahead of another).
+// Resident blocks per SM of the persistent launch.  Every barrier and grid-wide
+// sum costs more with more blocks; on GB300 (Q1 65^3 CN steps) 2 blocks of 256
+// threads per SM were fastest (2: 276 us per solve, 3: 298, 4: 316).
+constexpr int kFusedBlocksPerSM = 2;
+
+template <int NV>
+__device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& buf, GridBar* bar,
+                                          double (&tot)[NV]) {
+  const int G = gridDim.x;
+  double* pb = part + (size_t)buf * 2 * G;
+  block_sums_to<NV>(v, pb, G);
+  grid_barrier(bar);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) s += __ldcg(pb + q * G + b);
+    tot[q] = block_allsum(s);
+  }
+  buf ^= 1;
+}
+
+template <int KT, class T>
+__global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, double* sc, const T* __restrict__ B,
+                                                   const T* __restrict__ dinv, const double* __restrict__ rhs,
+                                                   double* xout, T* x, T* r, T* rh, T* pv, T* v, T* s, T* t, T* ph,
+                                                   T* sh, double* part, GridBar* bar) {
+  const int K = KT > 0 ? KT : of.K;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double atol = sc[S_ATOL], rtol = sc[S_RTOL];
+  const int maxit = (int)sc[S_MAXIT];
+  volatile int* berr = &bar->err;
+  int buf = 0;
+  double a1[1], t1[1], a2[2], t2[2];
+  // r = rhs, rhat = r, x = p = v = 0, rho = (r, r)
+  T a0 = 0;
+  for (int64_t i = i0; i < N; i += stride) {
+    const T ri = (T)rhs[i];
+    x[i] = 0;
+    r[i] = ri;
+    rh[i] = ri;
+    pv[i] = 0;
+    v[i] = 0;
+    a0 = fma(ri, ri, a0);
+  }
+  a1[0] = (double)a0;
+  grid_sums<1>(a1, part, buf, bar, t1);
+  double rho = t1[0];
+  const double n0 = sqrt(rho);
+  const double tol = fmax(atol, rtol * n0);
+  double alpha = 1.0, omega = 1.0, beta = 0.0, nres = n0;
+  int its = 0;
+  int done = !isfinite(n0) ? 2 : (n0 < tol ? 1 : (maxit <= 0 ? 4 : 0));
+  while (done == 0) {
+    // p = r + beta (p - omega v), phat = D^{-1} p
+    const T tb = (T)beta, to = (T)omega;
+    for (int64_t i = i0; i < N; i += stride) {
+      const T pi = r[i] + tb * (pv[i] - to * v[i]);
+      pv[i] = pi;
+      ph[i] = dinv[i] * pi;
+    }
+    grid_barrier(bar);
+    // v = B phat, alpha = rho / (rhat, v)
+    a0 = 0;
+    for (int64_t i = i0; i < N; i += stride) {
+      T y = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) y = fma(B[k * N + i], ph[i + of.o[k]], y);
+      v[i] = y;
+      a0 = fma(rh[i], y, a0);
+    }
+    a1[0] = (double)a0;
+    grid_sums<1>(a1, part, buf, bar, t1);
+    alpha = rho / t1[0];
+    if (!isfinite(alpha) || t1[0] == 0.0 || *berr) { done = 2; break; }
+    // s = r - alpha v, shat = D^{-1} s, ||s||
+    const T ta = (T)alpha;
+    a0 = 0;
+    for (int64_t i = i0; i < N; i += stride) {
+      const T si = r[i] - ta * v[i];
+      s[i] = si;
+      sh[i] = dinv[i] * si;
+      a0 = fma(si, si, a0);
+    }
+    a1[0] = (double)a0;
+    grid_sums<1>(a1, part, buf, bar, t1);
+    const double ns = sqrt(t1[0]);
+    if (!isfinite(ns) || *berr) { done = 2; break; }
+    if (ns < tol) {   // converged at s: x += alpha phat
+      for (int64_t i = i0; i < N; i += stride) x[i] = x[i] + ta * ph[i];
+      nres = ns;
+      ++its;
+      done = 1;
+      break;
+    }
+    // t = B shat, omega = (t, s) / (t, t)
+    T b0 = 0, b1 = 0;
+    for (int64_t i = i0; i < N; i += stride) {
+      T y = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) y = fma(B[k * N + i], sh[i + of.o[k]], y);
+      t[i] = y;
+      b0 = fma(y, s[i], b0);
+      b1 = fma(y, y, b1);
+    }
+    a2[0] = (double)b0;
+    a2[1] = (double)b1;
+    grid_sums<2>(a2, part, buf, bar, t2);
+    omega = t2[0] / t2[1];
+    if (!isfinite(omega) || t2[1] == 0.0 || *berr) { done = 2; break; }
+    // x += alpha phat + omega shat, r = s - omega t, ||r||, (rhat, r)
+    const T tom = (T)omega;
+    b0 = 0;
+    b1 = 0;
+    for (int64_t i = i0; i < N; i += stride) {
+      x[i] = x[i] + ta * ph[i] + tom * sh[i];
+      const T ri = s[i] - tom * t[i];
+      r[i] = ri;
+      b0 = fma(ri, ri, b0);
+      b1 = fma(rh[i], ri, b1);
+    }
+    a2[0] = (double)b0;
+    a2[1] = (double)b1;
+    grid_sums<2>(a2, part, buf, bar, t2);
+    nres = sqrt(t2[0]);
+    const double rho_old = rho;
+    rho = t2[1];
+    beta = (rho / rho_old) * (alpha / omega);
+    ++its;
+    if (!isfinite(nres) || *berr) done = 2;
+    else if (nres < tol) done = 1;
+    else if (its >= maxit) done = 4;
+  }
+  for (int64_t i = i0; i < N; i += stride) xout[i] = (double)x[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[S_N0] = n0;
+    sc[S_NRES] = nres;
+    sc[S_ITS] = (double)its;
+    sc[S_ALPHA] = alpha;
+    sc[S_OMEGA] = omega;
+    sc[S_RHO] = rho;
+    sc[S_DONE] = *berr ? 2.0 : (double)done;
   }
 }
 
@@ -732,6 +889,7 @@ int ensure_work(afc_problem_s* p, int nvec, bool fp32) {
     int st = w.sc.alloc(S_END + 8);
     if (st) return st;
     if ((st = w.counter.alloc(4))) return st;
+    if ((st = w.barrier.alloc(4))) return st;
     if (cudaMallocHost((void**)&w.hsc, (S_END + 8) * sizeof(double)) != cudaSuccess) {
       set_error("cudaMallocHost failed");
       return AFC_E_OOM;
@@ -750,6 +908,56 @@ T* vec_at(KrylovWork& w, int q) {
   return reinterpret_cast<T*>(w.vec.base) + q * w.vstride + w.pad;
 }
 
+// The persistent BiCGStab launch on stream s (no synchronisation); *ok = false when
+// the device cannot run cooperative launches (the caller then takes the
+// kernel-per-phase path).
+template <class T>
+int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* dinv, const afc_opts* o,
+                      const double* rhs, double* xout, bool* ok) {
+  KrylovWork& w = *p->kw;
+  if (w.coop < 0) {
+    int c = 0;
+    AFC_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrCooperativeLaunch, p->device));
+    AFC_CUDA(cudaDeviceGetAttribute(&w.nsm, cudaDevAttrMultiProcessorCount, p->device));
+    w.coop = c;
+  }
+  *ok = w.coop > 0;
+  if (!*ok) return AFC_OK;
+  const int64_t N = p->N;
+  T *x = vec_at<T>(w, 0), *r = vec_at<T>(w, 1), *rh = vec_at<T>(w, 2), *pp = vec_at<T>(w, 3), *v = vec_at<T>(w, 4),
+    *sv = vec_at<T>(w, 5), *t = vec_at<T>(w, 6), *ph = vec_at<T>(w, 7), *sh = vec_at<T>(w, 8);
+  double* sc = w.sc.p;
+  GridBar* bar = reinterpret_cast<GridBar*>(w.barrier.p);
+  AFC_LAUNCH(p, "k_solver_reset", k_solver_reset<<<1, 32, 0, s>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
+  int st = AFC_OK;
+  with_K(p->K, [&](auto kc) {
+    constexpr int KT = decltype(kc)::value;
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicg_fused<KT, T>, kBlock, 0);
+    if (e != cudaSuccess || nb < 1) {
+      st = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "occupancy of k_bicg_fused");
+      return;
+    }
+    const int64_t want = (N + kBlock - 1) / kBlock;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::min(nb, kFusedBlocksPerSM) * w.nsm));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaEvent_t ev = prof_start(p);
+    e = cudaLaunchKernelEx(&cfg, k_bicg_fused<KT, T>, N, p->offs, sc, B, dinv, rhs, xout, x, r, rh, pp, v, sv, t, ph,
+                           sh, w.part.p, bar);
+    prof_stop(p, "k_bicg_fused", ev);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaLaunchKernelEx(k_bicg_fused)");
+  });
+  return st;
+}
+
 template <class T>
 int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
                   int* its, double* res) {
@@ -765,6 +973,25 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
   unsigned int* cnt = w.counter.p;
   const int G = kRedBlocks;
   const int64_t gr = grid_for(N);
+  bool fused = false;
+  if ((st = bicg_fused_launch<T>(p, s, B, dinv, o, rhs, xout, &fused))) return st;
+  if (fused) {
+    AFC_CUDA(cudaMemcpyAsync(w.hsc, sc, (S_MAXIT + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned int* hbar = reinterpret_cast<unsigned int*>(w.hsc + S_END);
+    AFC_CUDA(cudaMemcpyAsync(hbar, w.barrier.p, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    AFC_CUDA(cudaStreamSynchronize(s));
+    if (its) *its = (int)w.hsc[S_ITS];
+    if (res) *res = w.hsc[S_NRES];
+    if (hbar[2] != 0u) {
+      AFC_CUDA(cudaMemsetAsync(w.barrier.p, 0, 4 * sizeof(unsigned int), s));
+      AFC_CUDA(cudaStreamSynchronize(s));
+      set_error("a grid barrier of the BiCGStab launch gave up waiting");
+      return AFC_E_TIMEOUT;
+    }
+    const double done = w.hsc[S_DONE];
+    if (done == 2.0) { set_error("BiCGStab breakdown or non-finite value"); return AFC_E_NAN; }
+    return done == 1.0 ? AFC_OK : AFC_NOT_CONVERGED;
+  }
   AFC_LAUNCH(p, "k_solver_reset", k_solver_reset<<<1, 32, 0, s>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
   AFC_LAUNCH(p, "k_bicg_init", k_bicg_init<T><<<G, kBlock, 0, s>>>(N, rhs, x, r, rh, pp, v, part, cnt, sc));
   AFC_CUDA(cudaGetLastError());
@@ -870,6 +1097,21 @@ int bicgstab_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* 
   unsigned int* cnt = w.counter.p;
   const int G = kRedBlocks;
   const int64_t gr = grid_for(N);
+  if (w.coop < 0) {
+    int c = 0;
+    AFC_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrCooperativeLaunch, p->device));
+    AFC_CUDA(cudaDeviceGetAttribute(&w.nsm, cudaDevAttrMultiProcessorCount, p->device));
+    w.coop = c;
+  }
+  if (w.coop > 0) {   // the whole solve is one persistent launch: no loop node needed
+    return capture_into(p, cs, g, frontier, [&]() -> int {
+      bool ok = false;
+      int s2 = bicg_fused_launch<T>(p, p->stream, B, dinv, o, rhs, xout, &ok);
+      if (s2) return s2;
+      AFC_CUDA(cudaGetLastError());
+      return AFC_OK;
+    }, frontier);
+  }
   GraphCond cond;
   cond.use = true;
   AFC_CUDA(cudaGraphConditionalHandleCreate(&cond.h, g, 0, 0));
