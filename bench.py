@@ -163,10 +163,10 @@ def _timed_steps(P, opts, steps, flush, stream, torch):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# (profiles/k_bicg_spmv2_q1_65.md), valid while the kernel's sources hash as they did then.
+# (profiles/k_bicg_fused_q1_65.md), valid while the kernel's sources hash as they did then.
 _NCU_TRAFFIC = {
-    "k_bicg_spmv2": {"bytes": 64.21e6, "sha1": "f38092f2cdd2bcab",
-                     "sources": ("krylov.cu", "kernels_common.cuh", "afc_internal.h")},
+    "k_bicg_fused": {"bytes": 73.91e6, "sha1": "09afaf9dc2fab183",
+                     "sources": ("krylov.cu", "kernels_common.cuh", "afc_internal.h", "grid_sync.cuh")},
 }
 
 
