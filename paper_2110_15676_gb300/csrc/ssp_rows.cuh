@@ -126,15 +126,56 @@ __device__ __forceinline__ void ssp_factors_row(const Offsets& of, const SspArra
   const double uti = a.ut[i];
   double Pp = 0.0, Pm = 0.0;
   long long kmax = dkey(uti), kmin = kmax;
+  if (MIXED) {
+    // The fluxes are floats: P+ and P- are summed exactly in 64-bit fixed point scaled
+    // to the row's largest flux (its 24-bit mantissa at bits 33..56, so 62 pairs cannot
+    // overflow), then rounded once to double.  This is at least as accurate as a double
+    // sum and runs on the integer pipe instead of two FP64 adds per pair.
+    constexpr int KA = KT > 0 ? KT : kMaxOffsets;
+    unsigned fb[KA];
+    unsigned emax = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (k == Kup || !((mk >> k) & 1ull)) continue;
-    const double r = ssp_flux<KT, MIXED>(of, a, k, i);
-    if (gt0(r)) Pp += r;
-    else if (!is0(r)) Pm += r;
-    const long long kj = dkey(a.ut[i + of.o[k]]);
-    kmax = kj > kmax ? kj : kmax;
-    kmin = kj < kmin ? kj : kmin;
+    for (int k = 0; k < K; ++k) {
+      fb[k] = 0u;
+      if (k == Kup || !((mk >> k) & 1ull)) continue;
+      unsigned b;
+      if (k > Kup) b = __float_as_uint(a.r32[(int64_t)(k - Kup - 1) * a.N + i]);
+      else b = __float_as_uint(a.r32[(int64_t)(Kup - 1 - k) * a.N + i + of.o[k]]) ^ 0x80000000u;   // r_ij = -r_ji
+      fb[k] = b;
+      const unsigned e = (b >> 23) & 0xffu;
+      emax = e > emax ? e : emax;
+      const long long kj = dkey(a.ut[i + of.o[k]]);
+      kmax = kj > kmax ? kj : kmax;
+      kmin = kj < kmin ? kj : kmin;
+    }
+    if (emax > 0u) {
+      long long sp = 0, sm = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const unsigned b = fb[k];
+        const int e = (int)((b >> 23) & 0xffu);
+        if (e == 0) continue;                       // zero or subnormal: widened to 0 as well
+        const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+        const int sh = e - (int)emax + 33;
+        const long long v = sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0LL);
+        if (b & 0x80000000u) sm += v;
+        else sp += v;
+      }
+      const double scale = __longlong_as_double((long long)((int)emax - 127 - 56 + 1023) << 52);   // 2^(emax-183)
+      Pp = (double)sp * scale;
+      Pm = -((double)sm * scale);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (k == Kup || !((mk >> k) & 1ull)) continue;
+      const double r = ssp_flux<KT, MIXED>(of, a, k, i);
+      if (gt0(r)) Pp += r;
+      else if (!is0(r)) Pm += r;
+      const long long kj = dkey(a.ut[i + of.o[k]]);
+      kmax = kj > kmax ? kj : kmax;
+      kmin = kj < kmin ? kj : kmin;
+    }
   }
   // >= 0 and <= 0: the max / min include i itself
   const double Qp = from_key(kmax) - uti, Qm = from_key(kmin) - uti;
