@@ -6,8 +6,10 @@
 // later barrier of the launch passes at once, so the launch still ends; the host
 // reads the flag and reports AFC_E_TIMEOUT.
 //
-// Memory: every thread fences its writes before arriving and after leaving, so
-// plain loads after the barrier see what other blocks wrote before it.  Arrays
+// Memory: the block's threads meet at __syncthreads, then its first thread fences
+// (cumulatively for the block's writes), arrives, waits and fences again before the
+// block's threads meet once more, so plain loads after the barrier see what other
+// blocks wrote before it.  Arrays
 // written inside a persistent launch must not be read through the read-only
 // (non-coherent) path, i.e. not through const __restrict__ pointers.
 #pragma once
@@ -32,7 +34,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 __device__ __forceinline__ void grid_barrier(GridBar* gb) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &gb->gen;
@@ -52,13 +53,11 @@ __device__ __forceinline__ void grid_barrier(GridBar* gb) {
           atomicExch(&gb->err, 1);
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
   }
   __syncthreads();
-  __threadfence();
 }
 
 }  // namespace afc
