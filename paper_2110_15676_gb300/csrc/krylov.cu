@@ -186,7 +186,7 @@ constexpr int kOrthQ = kMaxRestart;
 // device scalar slots
 enum : int {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_TOL, S_NRES, S_N0, S_ITS, S_DONE, S_MAXIT,
-  S_BETA, S_K_USED, S_INVH, S_CYCLE_DONE, S_FIRST, S_ATOL, S_RTOL,
+  S_BETA, S_K_USED, S_INVH, S_CYCLE_DONE, S_FIRST, S_ATOL, S_RTOL, S_NO_REORTH,
   S_CS = 20, S_SN = S_CS + kMaxRestart, S_G = S_SN + kMaxRestart, S_Y = S_G + kMaxRestart + 1,
   S_H1 = S_Y + kMaxRestart, S_H2 = S_H1 + kMaxRestart + 1, S_HCOL = S_H2 + kMaxRestart + 1,
   S_END = S_HCOL + (kMaxRestart + 1) * kMaxRestart
@@ -690,12 +690,23 @@ __global__ void k_gm_spmv(int64_t N, Offsets of, const double* __restrict__ sc, 
 // A thread owns elements and holds all k + 1 running dots in registers (QMAX is the
 // compile-time bound on k + 1, the loops over q are unrolled and predicated), so each
 // element's k + 1 basis values are independent loads in flight together.
+//
+// Three launches per Arnoldi step: (1) h1 = V^T w and ||w||^2; (2) w -= V h1 and
+// h2 = V^T w (the re-orthogonalisation); (3) w -= V h2, ||w||, and the Hessenberg
+// column.  The last block of (1) applies the DGKS test: if ||w - V h1|| >= ||w|| / sqrt(2)
+// (with ||w - V h1||^2 = ||w||^2 - ||h1||^2 for orthonormal V) little of w lay in the
+// basis, the second projection would change nothing worth keeping, and (2) takes the
+// role of (3) directly (h2 = 0) while (3) does nothing.
 template <class T, int QMAX>
 __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int outslot,
                                                  T* __restrict__ w, const T* __restrict__ V, size_t vstride,
                                                  double* __restrict__ part, int64_t pstride, unsigned int* counter) {
   if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
-  const bool want_norm = outslot < 0;
+  const bool first = hslot < 0;                               // launch (1)
+  const bool no_reorth = !first && sc[S_NO_REORTH] != 0.0;
+  if (no_reorth && outslot < 0) return;                       // launch (3) has nothing to do
+  const bool want_norm = outslot < 0 || no_reorth;
+  if (want_norm && no_reorth) outslot = -1;
   __shared__ T hs[QMAX];
   for (int q = threadIdx.x; q < QMAX; q += blockDim.x) hs[q] = (hslot >= 0 && q <= k) ? (T)sc[hslot + q] : (T)0;
   __syncthreads();
@@ -721,20 +732,26 @@ __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, i
 #pragma unroll
       for (int q = 0; q < QMAX; ++q)
         if (q <= k) acc[q] = fma(wi, v[q], acc[q]);
+      if (first) nrm = fma(wi, wi, nrm);
     }
   }
-  const int nq = want_norm ? 1 : k + 1;
+  // sums: the k + 1 dots (and ||w||^2 as sum k + 1 in launch (1)), or the norm alone
+  const int nq = want_norm ? 1 : (first ? k + 2 : k + 1);
   if (want_norm) {
     const double t = block_allsum((double)nrm);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
   } else {
-    __shared__ double red[kBlock / 32][QMAX];
+    __shared__ double red[kBlock / 32][QMAX + 1];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
       if (q > k) break;
       const T t = warp_sum(acc[q]);
       if (lane == 0) red[wp][q] = (double)t;
+    }
+    if (first) {
+      const T t = warp_sum(nrm);
+      if (lane == 0) red[wp][k + 1] = (double)t;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
@@ -754,7 +771,7 @@ __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, i
   if (!am_last) return;
   __threadfence();
   // totals of the nq sums: warp q' takes q = q', q' + 8, ... (block order, fixed)
-  __shared__ double tot[QMAX];
+  __shared__ double tot[QMAX + 1];
   {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int q = wp; q < nq; q += nwarp) {
@@ -768,7 +785,16 @@ __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, i
   if (threadIdx.x != 0) return;
   *counter = 0u;
   if (!want_norm) {
-    for (int q = 0; q < nq; ++q) sc[outslot + q] = tot[q];
+    for (int q = 0; q <= k; ++q) sc[outslot + q] = tot[q];
+    if (first) {   // DGKS test: re-orthogonalise only if ||w - V h1||^2 < ||w||^2 / 2
+      double proj = 0.0;
+      for (int q = 0; q <= k; ++q) proj += tot[q] * tot[q];
+      const double ww = tot[k + 1], rest = ww - proj;
+      const bool skip = rest >= 0.5 * ww && ww > 0.0;
+      sc[S_NO_REORTH] = skip ? 1.0 : 0.0;
+      if (skip)
+        for (int q = 0; q <= k; ++q) sc[S_H2 + q] = 0.0;
+    }
     return;
   }
   const double hk1 = sqrt(tot[0]);
