@@ -229,8 +229,9 @@ def mc_sweep(afc, W, torch, flush, stream, reps, solve=True):
     # a realistic state of the fixed point: the iterate after a few damped corrections
     # from u0 (mixed-precision inner GMRES), not a random field
     P.set_solution(wl.u0)
+    # (host-driven loop: the same arithmetic as the graph, and its kernels stay visible to profilers)
     P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
-                                        ksp_rtol=1e-6, fp_fixed_its=6, precision=afc.AFC_MIXED))
+                                        ksp_rtol=1e-6, fp_fixed_its=6, precision=afc.AFC_MIXED, graph=0))
     info = P.info()
     N, nnz, E = info["n_nodes"], info["nnz"], info["n_edges"]
     for _ in range(3):
