@@ -53,6 +53,22 @@ def _peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
+def whole_job(units, ms, ws, device="cpu"):
+    """Whole-job throughput of N replicas: the units all ranks processed divided by the
+    slowest rank's time (MAX over ranks), in units per second; (value, max_ms).  With one
+    rank no process group is needed."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(units), float(ms)], dtype=torch.float64, device=device)
+        u = t[:1].clone()
+        m = t[1:].clone()
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        units, ms = float(u.item()), float(m.item())
+    return units / (ms / 1e3), ms
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -494,11 +510,7 @@ def run_ours(args, ws, rank, local):
     barrier()
     clk = clocks.stop()
     gpu_launches = P.launches() - launches0
-    t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = float(N) * its_total * ws / (ms_max / 1e3)
+    value, ms_max = whole_job(float(N) * its_total, ms_total, ws, device="cuda")
 
     # per-kernel device time: the same steps again, issued launch by launch (a CUDA graph's
     # nodes cannot carry events), with every launch bracketed by events on the stream
@@ -546,11 +558,8 @@ def run_ours(args, ws, rank, local):
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_its += st["outer_its"]
         host_u.copy_(out_u)
-    te = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": float(N) * e2e_its * ws / (float(te.item()) / 1e3), "unit": "dof-iters/s",
-           "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
+    e2e_value, _ = whole_job(float(N) * e2e_its, e2e_ms, ws, device="cuda")
+    e2e = {"value": e2e_value, "unit": "dof-iters/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
 
     sweep = None
     if not args.no_mc_sweep and args.steps > 0:
