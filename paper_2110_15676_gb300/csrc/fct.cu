@@ -139,14 +139,16 @@ __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __
   if (i >= N) return;
   if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
   const unsigned long long mk = mask[i];
-  double Pp = 0.0, Pm = 0.0;
+  constexpr int KA = KT > 0 ? KT : kMaxOffsets;
+  unsigned long long rb[KA];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (k == Kup || !((mk >> k) & 1ull)) continue;
-    const double r = pair_flux(of, Kup, k, i, N, r_up);
-    if (gt0(r)) Pp += r;
-    else if (!is0(r)) Pm += r;
+  for (int k = 0; k < KA; ++k) {
+    rb[k] = 0ull;
+    if (k >= K || k == Kup || !((mk >> k) & 1ull)) continue;
+    rb[k] = (unsigned long long)__double_as_longlong(pair_flux(of, Kup, k, i, N, r_up));
   }
+  double Pp, Pm;
+  exact_signed_sums<KA>(rb, K, Pp, Pm);
   const double m = mL[i];
   Rp[i] = zalesak_factor(m * Qp[i], dt * Pp);
   Rm[i] = zalesak_factor(m * Qm[i], dt * Pm);

@@ -62,6 +62,63 @@ __device__ __forceinline__ double widen_exact(float x) {
   return __longlong_as_double((long long)bits);
 }
 
+// Sums of the positive and of the negative values among n doubles (given as bit
+// patterns, 0 for absent entries), exact: every mantissa is placed in a 128-bit fixed
+// point scaled to the largest exponent (its mantissa at bits 64..116, so up to 2^10
+// terms cannot overflow), the words are added with carry on the integer pipe, and
+// each total is rounded to double once.  Subnormal inputs count as zero.  On GB300
+// this replaces two FP64 adds per value (an FP64 warp instruction occupies the pipe
+// for 16 cycles) with about a dozen integer instructions, and is more accurate.
+template <int KA>
+__device__ __forceinline__ void exact_signed_sums(const unsigned long long (&bits)[KA], int n, double& pos,
+                                                  double& neg) {
+  unsigned emax = 0;
+#pragma unroll
+  for (int k = 0; k < KA; ++k) {
+    if (k >= n) break;
+    const unsigned e = (unsigned)(bits[k] >> 52) & 0x7ffu;
+    emax = e > emax ? e : emax;
+  }
+  pos = 0.0;
+  neg = 0.0;
+  if (emax == 0u) return;
+  unsigned long long ph = 0, pl = 0, nh = 0, nl = 0;
+#pragma unroll
+  for (int k = 0; k < KA; ++k) {
+    if (k >= n) break;
+    const unsigned long long b = bits[k];
+    const int e = (int)((b >> 52) & 0x7ffu);
+    if (e == 0) continue;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = e - (int)emax + 64;
+    unsigned long long lo, hi;
+    if (sh >= 64) {
+      lo = 0ull;
+      hi = m;
+    } else if (sh > 0) {
+      lo = m << sh;
+      hi = m >> (64 - sh);
+    } else if (sh > -64) {
+      lo = m >> (-sh);
+      hi = 0ull;
+    } else {
+      lo = 0ull;
+      hi = 0ull;
+    }
+    if (b >> 63) {
+      nl += lo;
+      nh += hi + (nl < lo ? 1ull : 0ull);
+    } else {
+      pl += lo;
+      ph += hi + (pl < lo ? 1ull : 0ull);
+    }
+  }
+  const double two64 = 18446744073709551616.0;
+  const int ex = (int)emax - 1139;   // value = fixed point * 2^(emax - 1023 - 52 - 64)
+  pos = scalbn(fma(__ull2double_rn(ph), two64, __ull2double_rn(pl)), ex);
+  neg = -scalbn(fma(__ull2double_rn(nh), two64, __ull2double_rn(nl)), ex);
+}
+
 // min / max of two values known to be >= 0 (correction factors, bounds): plain int compare
 __device__ __forceinline__ double imin_nn(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
