@@ -578,6 +578,16 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_its)
 
+    # every profiled kernel with its algorithmic FP64 work: achieved rate and fraction of the pipe
+    kernel_table = {}
+    for k, (kms_k, kc_k) in sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]:
+        row = {"ms": kms_k, "launches": kc_k, "share": kms_k / tot_ms}
+        b_k, w_k, _ = _kernel_work(k, N, nnz, E, p_inner / max(kc_k, 1))
+        if b_k == "alu":
+            ach = w_k / (kms_k / kc_k / 1e3) / 1e12
+            row.update({"bound": "alu", "achieved_tflops": ach, "frac": ach / FP64_PEAK_TFLOPS})
+        kernel_table[k] = row
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "dof-iters/s", "n_gpus": ws, "steps": args.steps,
@@ -587,8 +597,7 @@ def run_ours(args, ws, rank, local):
                        "fixed_point_its": its_total, "krylov_its": inner_total,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
-            "kernels": {k: {"ms": v[0], "launches": v[1]}
-                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]},
+            "kernels": kernel_table,
             "kernel_times": "second pass of the same steps, launches issued one by one with per-launch CUDA "
                             "events (the timed pass runs each step as one CUDA graph)",
             "mixed": mixed, "mc_sweep": sweep, "batched": bat, "serving": srv, "cpu_baseline": cpu,
