@@ -158,7 +158,7 @@ __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __
 // res = b0 + F* - (m/dt u + AA u / 2) on free rows, 0 on Dirichlet rows;
 // block partial sums of res^2 for the stopping test.
 template <int KT>
-__global__ void __launch_bounds__(256, 3) k_cn_residual(int64_t N, Offsets of, int limiter, const unsigned long long* __restrict__ mask,
+__global__ void __launch_bounds__(256, 4) k_cn_residual(int64_t N, Offsets of, int limiter, const unsigned long long* __restrict__ mask,
                               const double* __restrict__ r_up, const double* __restrict__ AA,
                               const double* __restrict__ un, const double* __restrict__ Rp,
                               const double* __restrict__ Rm, const double* __restrict__ b0,
