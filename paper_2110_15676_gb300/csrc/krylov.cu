@@ -456,19 +456,44 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
 // threads per SM were fastest (2: 276 us per solve, 3: 298, 4: 316).
 constexpr int kFusedBlocksPerSM = 2;
 
+// Grid-wide sums of NV <= 2 values per thread.  Warp q forms the block's sum of
+// value q (a column sum in the order of warp0_column_sum) and stores it at
+// part[q * G + block]; after the barrier warp q of every block reads the G partials
+// of value q, lane l summing blocks l, l + 32, ... in turn before a butterfly over
+// the lanes.  Every block runs the same operations on the same partials, so all
+// obtain the same totals bit for bit.  The two sums of NV = 2 run in two warps at
+// once, and the only block-wide meeting after the barrier is the one that hands
+// the totals on (the totals alternate between two shared slots, like the partials,
+// so a later call cannot overwrite a slot that a thread still reads).
 template <int NV>
 __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& buf, GridBar* bar,
                                           double (&tot)[NV]) {
+  static_assert(NV >= 1 && NV <= 2, "two partial buffers of 2 G values");
+  __shared__ double col[NV][kBlock];
+  __shared__ double shtot[2][NV];
   const int G = gridDim.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* pb = part + (size_t)buf * 2 * G;
-  block_sums_to<NV>(v, pb, G);
-  grid_barrier(bar);
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < G; b += blockDim.x) s += __ldcg(pb + q * G + b);
-    tot[q] = block_allsum(s);
+  for (int q = 0; q < NV; ++q) col[q][threadIdx.x] = v[q];
+  __syncthreads();
+  if (w < NV) {
+    double t = col[w][lane];
+    for (int j = lane + 32; j < kBlock; j += 32) t += col[w][j];
+    t = warp_sum(t);
+    if (lane == 0) pb[w * G + blockIdx.x] = t;
   }
+  grid_barrier(bar);   // begins with __syncthreads: col is free again after it
+  if (w < NV) {
+    double t = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < G; b += 32) t += __ldcg(pb + w * G + b);
+    t = warp_sum(t);
+    if (lane == 0) shtot[buf][w] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = shtot[buf][q];
   buf ^= 1;
 }
 
