@@ -180,6 +180,8 @@ int fe_stage(afc_problem_s* p, const double* uin, double dt, int limiter, double
 int ensure_ssp_mixed(afc_problem_s* p);   // single-precision copies of m_ij, d_ij for the mixed stage
 struct SspArrays;
 SspArrays ssp_arrays(afc_problem_s* p);
+// The residual functions below store ||res||^2 at *normsq_slot; with a null slot they
+// leave the grid_for(N) block partials of res^2 in p->part for the caller to sum.
 // CN helpers
 int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
 int cn_linear_guess(afc_problem_s* p, const double* u_old, double* u);             // u = 2 ut - u_old (after cn_predictor)

@@ -140,15 +140,14 @@ __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __
   if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
   const unsigned long long mk = mask[i];
   constexpr int KA = KT > 0 ? KT : kMaxOffsets;
-  unsigned long long rb[KA];
+  SignedFixedSums acc;
 #pragma unroll
   for (int k = 0; k < KA; ++k) {
-    rb[k] = 0ull;
     if (k >= K || k == Kup || !((mk >> k) & 1ull)) continue;
-    rb[k] = (unsigned long long)__double_as_longlong(pair_flux(of, Kup, k, i, N, r_up));
+    acc.add((unsigned long long)__double_as_longlong(pair_flux(of, Kup, k, i, N, r_up)));
   }
   double Pp, Pm;
-  exact_signed_sums<KA>(rb, K, Pp, Pm);
+  acc.result(Pp, Pm);
   const double m = mL[i];
   Rp[i] = zalesak_factor(m * Qp[i], dt * Pp);
   Rm[i] = zalesak_factor(m * Qm[i], dt * Pm);
@@ -408,7 +407,7 @@ int mc_cn_residual(afc_problem_s* p, const double* u, double* res, double* norms
                                                         p->b0.p, p->mLdt.p, p->dir.p, res, p->Fs.p, p->part.p));
   });
   if (st) return st;
-  finalize_sum(p, p->part.p, (int)g, normsq_slot);
+  if (normsq_slot) finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
@@ -432,7 +431,7 @@ int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int li
                                                       p->Rp.p, p->Rm.p, p->b0.p, p->mLdt.p, p->dir.p, res, p->Fs.p,
                                                       p->part.p));
   });
-  finalize_sum(p, p->part.p, (int)g, normsq_slot);
+  if (normsq_slot) finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }

@@ -38,8 +38,14 @@ __global__ void k_fp_init(double* sc, double thresh, int fixed, int maxit) {
   sc[F_REVAL] = 0.0;
 }
 
-// After a residual evaluation: R = ||res||; stop or solve.
-__global__ void k_fp_control(double* sc, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_solve) {
+// After a residual evaluation: R = ||res||; stop or solve.  The residual pass leaves
+// its block partials of res^2 in part[0 .. npart); one block of 1024 threads sums them
+// (the order of finalize_sum) before the decision, so the sum needs no launch of its own.
+__global__ void k_fp_control(double* sc, const double* __restrict__ part, int npart,
+                             cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_solve) {
+  double v = 0.0;
+  for (int q = threadIdx.x; q < npart; q += blockDim.x) v += part[q];
+  block_sum_to(v, sc + F_NORMSQ);   // a single block: sc[F_NORMSQ]
   if (threadIdx.x != 0) return;
   const double R = sqrt(sc[F_NORMSQ]);
   const double it = sc[F_CORR];
@@ -227,7 +233,8 @@ int build_fixed_point(afc_problem_s* p, const afc_opts* o, int system, Pro prolo
       return capture_into(p, cs, body, {}, [&]() -> int {
         int s = residual();
         if (s) return s;
-        AFC_LAUNCH(p, "k_fp_control", k_fp_control<<<1, 32, 0, p->stream>>>(p->scal.p, h_loop, h_solve));
+        AFC_LAUNCH(p, "k_fp_control", k_fp_control<<<1, 1024, 0, p->stream>>>(p->scal.p, p->part.p,
+                                                                               (int)grid_for(p->N), h_loop, h_solve));
         AFC_CUDA(cudaGetLastError());
         return AFC_OK;
       }, bf);
@@ -330,8 +337,8 @@ int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
           return cn_update(p, 0.0, nullptr, p->u.p, p->u0.p);
         },
         [&]() -> int {
-          if (lim == AFC_LIM_MC) return mc_cn_residual(p, p->u.p, p->res.p, p->scal.p);
-          return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, p->scal.p);
+          if (lim == AFC_LIM_MC) return mc_cn_residual(p, p->u.p, p->res.p, nullptr);
+          return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, nullptr);
         },
         [&]() -> int {
           if (lim == AFC_LIM_MC) return axpy_device(p, o->omega, p->delta.p, p->u.p);
@@ -360,7 +367,7 @@ int stationary_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
           AFC_CUDA(cudaGetLastError());
           return AFC_OK;
         },
-        [&]() -> int { return mc_limited_residual(p, p->u.p, lim, p->res.p, p->scal.p); },
+        [&]() -> int { return mc_limited_residual(p, p->u.p, lim, p->res.p, nullptr); },
         [&]() -> int { return axpy_device(p, o->omega, p->delta.p, p->u.p); }, *p->g_stat);
     if (st) {
       drop(p->g_stat);

@@ -119,6 +119,75 @@ __device__ __forceinline__ void exact_signed_sums(const unsigned long long (&bit
   neg = -scalbn(fma(__ull2double_rn(nh), two64, __ull2double_rn(nl)), ex);
 }
 
+// The same sums, taken one value at a time so that no value has to be kept: the
+// totals are held in 128-bit fixed point scaled to the largest exponent seen so far,
+// and a value with a larger exponent first shifts both totals right (the bits that
+// leave the 128-bit range are below 2^-64 of the new largest value's last bit).
+// Values only move in and out of registers once, which keeps a row of 26 pair
+// fluxes from holding 52 registers until its largest exponent is known.
+struct SignedFixedSums {
+  unsigned emax = 0u;
+  unsigned long long ph = 0ull, pl = 0ull, nh = 0ull, nl = 0ull;
+
+  __device__ static __forceinline__ void shr128(unsigned long long& h, unsigned long long& l, unsigned d) {
+    if (d >= 128u) {
+      h = 0ull;
+      l = 0ull;
+    } else if (d >= 64u) {
+      l = h >> (d - 64u);
+      h = 0ull;
+    } else {
+      l = (l >> d) | (h << (64u - d));
+      h >>= d;
+    }
+  }
+  __device__ __forceinline__ void add(unsigned long long b) {
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e == 0u) return;
+    if (e > emax) {
+      if (emax != 0u) {
+        shr128(ph, pl, e - emax);
+        shr128(nh, nl, e - emax);
+      }
+      emax = e;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = (int)e - (int)emax + 64;   // <= 64
+    unsigned long long lo, hi;
+    if (sh >= 64) {
+      lo = 0ull;
+      hi = m;
+    } else if (sh > 0) {
+      lo = m << sh;
+      hi = m >> (64 - sh);
+    } else if (sh > -64) {
+      lo = m >> (-sh);
+      hi = 0ull;
+    } else {
+      lo = 0ull;
+      hi = 0ull;
+    }
+    if (b >> 63) {
+      nl += lo;
+      nh += hi + (nl < lo ? 1ull : 0ull);
+    } else {
+      pl += lo;
+      ph += hi + (pl < lo ? 1ull : 0ull);
+    }
+  }
+  __device__ __forceinline__ void result(double& pos, double& neg) const {
+    if (emax == 0u) {
+      pos = 0.0;
+      neg = 0.0;
+      return;
+    }
+    const double two64 = 18446744073709551616.0;
+    const int ex = (int)emax - 1139;
+    pos = scalbn(fma(__ull2double_rn(ph), two64, __ull2double_rn(pl)), ex);
+    neg = -scalbn(fma(__ull2double_rn(nh), two64, __ull2double_rn(nl)), ex);
+  }
+};
+
 // min / max of two values known to be >= 0 (correction factors, bounds): plain int compare
 __device__ __forceinline__ double imin_nn(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;

@@ -451,10 +451,14 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
 // The order is the same in every block, so every block obtains the same totals
 // bit for bit and takes the same branches.  Partials alternate between two buffers
 // (a block can run at most one reduction ahead of another).
-// Resident blocks per SM of the persistent launch.  Every barrier and grid-wide
-// sum costs more with more blocks; on GB300 (Q1 65^3 CN steps) 2 blocks of 256
-// threads per SM were fastest (2: 276 us per solve, 3: 298, 4: 316).
-constexpr int kFusedBlocksPerSM = 2;
+// Shape of the persistent launch: one block of 512 threads per SM.  Every barrier
+// and grid-wide sum costs more with more blocks.  On GB300 (Q1 65^3, 27 offsets,
+// per BiCGStab iteration) 512 x 1 per SM took 62.4 us, 256 x 2 66.0 us, 1024 x 1
+// 65.9 us, 256 x 1 72.1 us, 128 x 4 77.0 us; earlier, 256 x 3 and 256 x 4 were
+// 8 % and 14 % slower than 256 x 2.  Block b owns the contiguous rows
+// [N b / G, N (b + 1) / G), which balances the blocks to one row.
+constexpr int kFusedBlock = 512;
+constexpr int kFusedBlocksPerSM = 1;
 
 // Grid-wide sums of NV <= 2 values per thread.  Warp q forms the block's sum of
 // value q (a column sum in the order of warp0_column_sum) and stores it at
@@ -469,7 +473,7 @@ template <int NV>
 __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& buf, GridBar* bar,
                                           double (&tot)[NV]) {
   static_assert(NV >= 1 && NV <= 2, "two partial buffers of 2 G values");
-  __shared__ double col[NV][kBlock];
+  __shared__ double col[NV][kFusedBlock];
   __shared__ double shtot[2][NV];
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -479,7 +483,7 @@ __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& bu
   __syncthreads();
   if (w < NV) {
     double t = col[w][lane];
-    for (int j = lane + 32; j < kBlock; j += 32) t += col[w][j];
+    for (int j = lane + 32; j < kFusedBlock; j += 32) t += col[w][j];
     t = warp_sum(t);
     if (lane == 0) pb[w * G + blockIdx.x] = t;
   }
@@ -498,21 +502,21 @@ __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& bu
 }
 
 template <int KT, class T>
-__global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, double* sc, const T* __restrict__ B,
+__global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(int64_t N, Offsets of, double* sc, const T* __restrict__ B,
                                                    const T* __restrict__ dinv, const double* __restrict__ rhs,
                                                    double* xout, T* x, T* r, T* rh, T* pv, T* v, T* s, T* t, T* ph,
-                                                   T* sh, double* part, GridBar* bar) {
+                                                   T* sh, double* part, GridBar* bar, double atol, double rtol,
+                                                   int maxit) {
   const int K = KT > 0 ? KT : of.K;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double atol = sc[S_ATOL], rtol = sc[S_RTOL];
-  const int maxit = (int)sc[S_MAXIT];
+  const int64_t G = gridDim.x;
+  const int64_t stride = kFusedBlock;
+  const int64_t i0 = N * blockIdx.x / G + threadIdx.x, iend = N * (blockIdx.x + 1) / G;
   volatile int* berr = &bar->err;
   int buf = 0;
   double a1[1], t1[1], a2[2], t2[2];
   // r = rhs, rhat = r, x = p = v = 0, rho = (r, r)
   T a0 = 0;
-  for (int64_t i = i0; i < N; i += stride) {
+  for (int64_t i = i0; i < iend; i += stride) {
     const T ri = (T)rhs[i];
     x[i] = 0;
     r[i] = ri;
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
   while (done == 0) {
     // p = r + beta (p - omega v), phat = D^{-1} p
     const T tb = (T)beta, to = (T)omega;
-    for (int64_t i = i0; i < N; i += stride) {
+    for (int64_t i = i0; i < iend; i += stride) {
       const T pi = r[i] + tb * (pv[i] - to * v[i]);
       pv[i] = pi;
       ph[i] = dinv[i] * pi;
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
     grid_barrier(bar);
     // v = B phat, alpha = rho / (rhat, v)
     a0 = 0;
-    for (int64_t i = i0; i < N; i += stride) {
+    for (int64_t i = i0; i < iend; i += stride) {
       T y = 0;
 #pragma unroll
       for (int k = 0; k < K; ++k) y = fma(B[k * N + i], ph[i + of.o[k]], y);
@@ -554,7 +558,7 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
     // s = r - alpha v, shat = D^{-1} s, ||s||
     const T ta = (T)alpha;
     a0 = 0;
-    for (int64_t i = i0; i < N; i += stride) {
+    for (int64_t i = i0; i < iend; i += stride) {
       const T si = r[i] - ta * v[i];
       s[i] = si;
       sh[i] = dinv[i] * si;
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
     const double ns = sqrt(t1[0]);
     if (!isfinite(ns) || *berr) { done = 2; break; }
     if (ns < tol) {   // converged at s: x += alpha phat
-      for (int64_t i = i0; i < N; i += stride) x[i] = x[i] + ta * ph[i];
+      for (int64_t i = i0; i < iend; i += stride) x[i] = x[i] + ta * ph[i];
       nres = ns;
       ++its;
       done = 1;
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
     }
     // t = B shat, omega = (t, s) / (t, t)
     T b0 = 0, b1 = 0;
-    for (int64_t i = i0; i < N; i += stride) {
+    for (int64_t i = i0; i < iend; i += stride) {
       T y = 0;
 #pragma unroll
       for (int k = 0; k < K; ++k) y = fma(B[k * N + i], sh[i + of.o[k]], y);
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
     const T tom = (T)omega;
     b0 = 0;
     b1 = 0;
-    for (int64_t i = i0; i < N; i += stride) {
+    for (int64_t i = i0; i < iend; i += stride) {
       x[i] = x[i] + ta * ph[i] + tom * sh[i];
       const T ri = s[i] - tom * t[i];
       r[i] = ri;
@@ -609,8 +613,15 @@ __global__ void __launch_bounds__(256, 4) k_bicg_fused(int64_t N, Offsets of, do
     else if (nres < tol) done = 1;
     else if (its >= maxit) done = 4;
   }
-  for (int64_t i = i0; i < N; i += stride) xout[i] = (double)x[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  for (int64_t i = i0; i < iend; i += stride) xout[i] = (double)x[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // the solver scalars, as the kernel-per-phase form leaves them
+    sc[S_ATOL] = atol;
+    sc[S_RTOL] = rtol;
+    sc[S_MAXIT] = (double)maxit;
+    sc[S_FIRST] = 1.0;
+    sc[S_K_USED] = 0.0;
+    sc[S_CYCLE_DONE] = 0.0;
+    sc[S_TOL] = tol;
     sc[S_N0] = n0;
     sc[S_NRES] = nres;
     sc[S_ITS] = (double)its;
@@ -979,21 +990,20 @@ int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* din
     *sv = vec_at<T>(w, 5), *t = vec_at<T>(w, 6), *ph = vec_at<T>(w, 7), *sh = vec_at<T>(w, 8);
   double* sc = w.sc.p;
   GridBar* bar = reinterpret_cast<GridBar*>(w.barrier.p);
-  AFC_LAUNCH(p, "k_solver_reset", k_solver_reset<<<1, 32, 0, s>>>(sc, o->ksp_atol, o->ksp_rtol, o->ksp_maxit));
   int st = AFC_OK;
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicg_fused<KT, T>, kBlock, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicg_fused<KT, T>, kFusedBlock, 0);
     if (e != cudaSuccess || nb < 1) {
       st = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "occupancy of k_bicg_fused");
       return;
     }
-    const int64_t want = (N + kBlock - 1) / kBlock;
+    const int64_t want = (N + kFusedBlock - 1) / kFusedBlock;
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::min(nb, kFusedBlocksPerSM) * w.nsm));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)G);
-    cfg.blockDim = dim3(kBlock);
+    cfg.blockDim = dim3(kFusedBlock);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -1002,7 +1012,7 @@ int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* din
     cfg.numAttrs = 1;
     cudaEvent_t ev = prof_start(p);
     e = cudaLaunchKernelEx(&cfg, k_bicg_fused<KT, T>, N, p->offs, sc, B, dinv, rhs, xout, x, r, rh, pp, v, sv, t, ph,
-                           sh, w.part.p, bar);
+                           sh, w.part.p, bar, o->ksp_atol, o->ksp_rtol, o->ksp_maxit);
     prof_stop(p, "k_bicg_fused", ev);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaLaunchKernelEx(k_bicg_fused)");
   });

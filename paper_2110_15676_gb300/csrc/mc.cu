@@ -383,7 +383,7 @@ int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* 
                                                       p->f.p, p->dir.p, res, want_F ? p->Fs.p : nullptr,
                                                       p->part.p));
   });
-  finalize_sum(p, p->part.p, (int)g, normsq_slot);
+  if (normsq_slot) finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
