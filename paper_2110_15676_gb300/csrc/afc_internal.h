@@ -200,8 +200,21 @@ int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* 
 
 // ---- reductions and BLAS-1 (krylov.cu) ----
 int dot_device(afc_problem_s* p, const double* x, const double* y, double* out_slot);
+// An update that the persistent BiCGStab applies to the solution x in its last pass,
+// unless the solve broke down: u += omega x, then a = u - uo and s = u + uo (the
+// damped CN correction and the node sums of the next flux pass, bit for bit what
+// cn_update computes).  u == nullptr: none.
+struct KrylovEpilogue {
+  double omega = 0.0;
+  double* u = nullptr;
+  const double* uo = nullptr;
+  double* a = nullptr;
+  double* s = nullptr;
+};
+// *epi_done (if given) tells whether the solve applied *epi; when it did not, the
+// caller applies the update itself.
 int krylov_solve(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, int* its,
-                 double* res);
+                 double* res, const KrylovEpilogue* epi = nullptr, bool* epi_done = nullptr);
 int dia_spmv(afc_problem_s* p, const double* A, const double* x, double* y);
 int axpy_device(afc_problem_s* p, double a, const double* x, double* y);   // y += a x
 int minmax_device(afc_problem_s* p, const double* x, double* mn, double* mx);

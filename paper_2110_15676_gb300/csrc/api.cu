@@ -133,8 +133,11 @@ int finish_stats(afc_problem_s* p, afc_stats* st, int status) {
 
 // Damped fixed point of Sec. 4 in defect form: res = residual(u); stop if
 // ||res|| < sqrt(N) tol; solve B delta = res; u += omega delta.
+// With `epi`, a persistent BiCGStab applies the update in its last pass and update()
+// only runs where the solve did not.
 template <class Residual, class Update>
-int fixed_point(afc_problem_s* p, const afc_opts* o, int system, afc_stats* st, Residual residual, Update update) {
+int fixed_point(afc_problem_s* p, const afc_opts* o, int system, afc_stats* st, Residual residual, Update update,
+                const KrylovEpilogue* epi = nullptr) {
   const double thresh = std::sqrt((double)p->N) * o->fp_tol;
   int status = AFC_NOT_CONVERGED;
   for (int it = 0;; ++it) {
@@ -156,13 +159,14 @@ int fixed_point(afc_problem_s* p, const afc_opts* o, int system, afc_stats* st, 
     }
     int its = 0;
     double kres = 0;
-    e = krylov_solve(p, system, o, p->res.p, p->delta.p, &its, &kres);
+    bool applied = false;
+    e = krylov_solve(p, system, o, p->res.p, p->delta.p, &its, &kres, epi, &applied);
     if (e < 0) return e;
     if (st) {
       st->inner_its += its;
       st->outer_its += 1;
     }
-    if ((e = update())) return e;
+    if (!applied && (e = update())) return e;
   }
   return status;
 }
@@ -485,9 +489,15 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   }
   if ((st = cn_update(p, 0.0, nullptr, p->u.p, p->u0.p))) return st;
   const double dt = o->dt;
+  KrylovEpilogue epi;
+  epi.omega = o->omega;
+  epi.u = p->u.p;
+  epi.uo = p->u0.p;
+  epi.a = p->cn_a.p;
+  epi.s = p->cn_s.p;
   st = fixed_point(
       p, o, 1, stt, [&]() { return cn_limited_residual(p, p->u.p, dt, lim, o->prelimit, p->res.p, p->scal.p); },
-      [&]() { return cn_update(p, o->omega, p->delta.p, p->u.p, p->u0.p); });
+      [&]() { return cn_update(p, o->omega, p->delta.p, p->u.p, p->u0.p); }, &epi);
   if (st < 0) return st;
   return finish_stats(p, stt, st);
 }

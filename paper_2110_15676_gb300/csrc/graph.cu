@@ -192,7 +192,7 @@ struct ProfOff {   // no event records inside captured graphs; captured launches
 // epilogue.  `system` 1: CN step, 0: stationary.
 template <class Pro, class Res, class Upd>
 int build_fixed_point(afc_problem_s* p, const afc_opts* o, int system, Pro prologue, Res residual, Upd update,
-                      StepGraph& sg) {
+                      StepGraph& sg, const KrylovEpilogue* epi = nullptr) {
   if (!p->cap_stream) AFC_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   cudaStream_t cs = p->cap_stream;
   ProfOff po(p);
@@ -247,13 +247,16 @@ int build_fixed_point(afc_problem_s* p, const afc_opts* o, int system, Pro prolo
     // Krylov solve (its while node counts separately), update and counters
     std::vector<cudaGraphNode_t> sf;
     const int64_t l0 = p->launches;
-    if ((st = krylov_graph(p, system, o, p->res.p, p->delta.p, cs, sbody, sf))) break;
+    bool applied = false;   // the persistent BiCGStab applies the update itself
+    if ((st = krylov_graph(p, system, o, p->res.p, p->delta.p, cs, sbody, sf, epi, &applied))) break;
     const int64_t lk = p->launches - l0;
     const int64_t body_k = o->ksp == AFC_KSP_GMRES ? 3 + 5 * (int64_t)o->gmres_restart : 5;
     auto r3 = count([&]() -> int {
       return capture_into(p, cs, sbody, sf, [&]() -> int {
-        int s = update();
-        if (s) return s;
+        if (!applied) {
+          int s = update();
+          if (s) return s;
+        }
         AFC_LAUNCH(p, "k_fp_after_solve",
                    k_fp_after_solve<<<1, 32, 0, p->stream>>>(p->scal.p, krylov_scalars(p),
                                                              o->ksp == AFC_KSP_GMRES ? 1 : 0, krylov_cycles_slot()));
@@ -316,6 +319,12 @@ int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
     p->g_step = new StepGraph();
     const int lim = o->limiter;
     const double dt = o->dt;
+    KrylovEpilogue epi;
+    epi.omega = o->omega;
+    epi.u = p->u.p;
+    epi.uo = p->u0.p;
+    epi.a = p->cn_a.p;
+    epi.s = p->cn_s.p;
     int st = build_fixed_point(
         p, o, 1,
         [&]() -> int {
@@ -343,7 +352,7 @@ int cn_step_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
         [&]() -> int {
           if (lim == AFC_LIM_MC) return axpy_device(p, o->omega, p->delta.p, p->u.p);
           return cn_update(p, o->omega, p->delta.p, p->u.p, p->u0.p);
-        }, *p->g_step);
+        }, *p->g_step, lim == AFC_LIM_MC ? nullptr : &epi);
     if (st) {
       drop(p->g_step);
       return st;

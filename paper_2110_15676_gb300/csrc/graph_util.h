@@ -55,7 +55,8 @@ inline int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t>& de
 // Krylov solve of `system` appended to graph g after `frontier` (updated): the
 // solver's loop is a while node whose condition the iteration kernels keep.
 int krylov_graph(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, cudaStream_t cs,
-                 cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier);
+                 cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier, const KrylovEpilogue* epi = nullptr,
+                 bool* epi_done = nullptr);
 
 // device address of the solver scalars (iteration count at slot kKrylovItsSlot)
 const double* krylov_scalars(afc_problem_s* p);

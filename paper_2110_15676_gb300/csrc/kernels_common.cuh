@@ -229,7 +229,7 @@ __device__ __forceinline__ double minmod(double a, double b) {
 __device__ __forceinline__ double pair_flux(const Offsets& of, int Kup, int k, int64_t i, int64_t N,
                                             const double* __restrict__ r_up) {
   if (k > Kup) return r_up[(int64_t)(k - Kup - 1) * N + i];
-  return -r_up[(int64_t)(Kup - 1 - k) * N + i + of.o[k]];
+  return neg_bits(r_up[(int64_t)(Kup - 1 - k) * N + i + of.o[k]]);   // -r_e, sign bit on the integer pipe
 }
 
 template <class T>

@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
                                                    const T* __restrict__ dinv, const double* __restrict__ rhs,
                                                    double* xout, T* x, T* r, T* rh, T* pv, T* v, T* s, T* t, T* ph,
                                                    T* sh, double* part, GridBar* bar, double atol, double rtol,
-                                                   int maxit) {
+                                                   int maxit, KrylovEpilogue ep) {
   const int K = KT > 0 ? KT : of.K;
   const int64_t G = gridDim.x;
   const int64_t stride = kFusedBlock;
@@ -613,7 +613,20 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     else if (nres < tol) done = 1;
     else if (its >= maxit) done = 4;
   }
-  for (int64_t i = i0; i < iend; i += stride) xout[i] = (double)x[i];
+  if (ep.u != nullptr && done != 2) {
+    const double om = ep.omega;
+    for (int64_t i = i0; i < iend; i += stride) {
+      const double xi = (double)x[i];
+      xout[i] = xi;
+      const double ui = ep.u[i] + om * xi;
+      ep.u[i] = ui;
+      const double uoi = ep.uo[i];
+      ep.a[i] = ui - uoi;
+      ep.s[i] = ui + uoi;
+    }
+  } else {
+    for (int64_t i = i0; i < iend; i += stride) xout[i] = (double)x[i];
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {   // the solver scalars, as the kernel-per-phase form leaves them
     sc[S_ATOL] = atol;
     sc[S_RTOL] = rtol;
@@ -975,7 +988,7 @@ T* vec_at(KrylovWork& w, int q) {
 // kernel-per-phase path).
 template <class T>
 int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* dinv, const afc_opts* o,
-                      const double* rhs, double* xout, bool* ok) {
+                      const double* rhs, double* xout, bool* ok, const KrylovEpilogue* epi) {
   KrylovWork& w = *p->kw;
   if (w.coop < 0) {
     int c = 0;
@@ -1012,7 +1025,8 @@ int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* din
     cfg.numAttrs = 1;
     cudaEvent_t ev = prof_start(p);
     e = cudaLaunchKernelEx(&cfg, k_bicg_fused<KT, T>, N, p->offs, sc, B, dinv, rhs, xout, x, r, rh, pp, v, sv, t, ph,
-                           sh, w.part.p, bar, o->ksp_atol, o->ksp_rtol, o->ksp_maxit);
+                           sh, w.part.p, bar, o->ksp_atol, o->ksp_rtol, o->ksp_maxit,
+                           epi ? *epi : KrylovEpilogue{});
     prof_stop(p, "k_bicg_fused", ev);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaLaunchKernelEx(k_bicg_fused)");
   });
@@ -1021,7 +1035,7 @@ int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* din
 
 template <class T>
 int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
-                  int* its, double* res) {
+                  int* its, double* res, const KrylovEpilogue* epi, bool* epi_done) {
   int st = ensure_work(p, 9, sizeof(T) == 4);
   if (st) return st;
   KrylovWork& w = *p->kw;
@@ -1035,7 +1049,8 @@ int bicgstab_impl(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o
   const int G = kRedBlocks;
   const int64_t gr = grid_for(N);
   bool fused = false;
-  if ((st = bicg_fused_launch<T>(p, s, B, dinv, o, rhs, xout, &fused))) return st;
+  if ((st = bicg_fused_launch<T>(p, s, B, dinv, o, rhs, xout, &fused, epi))) return st;
+  if (epi_done) *epi_done = fused && epi != nullptr;
   if (fused) {
     AFC_CUDA(cudaMemcpyAsync(w.hsc, sc, (S_MAXIT + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
     unsigned int* hbar = reinterpret_cast<unsigned int*>(w.hsc + S_END);
@@ -1146,7 +1161,8 @@ namespace {
 
 template <class T>
 int bicgstab_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, const double* rhs, double* xout,
-                   cudaStream_t cs, cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier) {
+                   cudaStream_t cs, cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier,
+                   const KrylovEpilogue* epi, bool* epi_done) {
   int st = ensure_work(p, 9, sizeof(T) == 4);
   if (st) return st;
   KrylovWork& w = *p->kw;
@@ -1165,9 +1181,10 @@ int bicgstab_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* 
     w.coop = c;
   }
   if (w.coop > 0) {   // the whole solve is one persistent launch: no loop node needed
+    if (epi_done) *epi_done = epi != nullptr;
     return capture_into(p, cs, g, frontier, [&]() -> int {
       bool ok = false;
-      int s2 = bicg_fused_launch<T>(p, p->stream, B, dinv, o, rhs, xout, &ok);
+      int s2 = bicg_fused_launch<T>(p, p->stream, B, dinv, o, rhs, xout, &ok, epi);
       if (s2) return s2;
       AFC_CUDA(cudaGetLastError());
       return AFC_OK;
@@ -1278,7 +1295,9 @@ int gmres_graph(afc_problem_s* p, const T* B, const T* dinv, const afc_opts* o, 
 }  // namespace
 
 int krylov_graph(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, cudaStream_t cs,
-                 cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier) {
+                 cudaGraph_t g, std::vector<cudaGraphNode_t>& frontier, const KrylovEpilogue* epi,
+                 bool* epi_done) {
+  if (epi_done) *epi_done = false;
   const bool mixed = o->precision == AFC_MIXED;
   if (mixed && p->precision != AFC_MIXED) {
     set_error("mixed-precision solve needs afc_assemble(..., AFC_MIXED)");
@@ -1289,12 +1308,12 @@ int krylov_graph(afc_problem_s* p, int system, const afc_opts* o, const double* 
     const float* B = system == 0 ? p->Bst32.p : p->Bcn32.p;
     const float* di = system == 0 ? p->dinv_st32.p : p->dinv_cn32.p;
     return gm ? gmres_graph<float>(p, B, di, o, rhs, x, cs, g, frontier)
-              : bicgstab_graph<float>(p, B, di, o, rhs, x, cs, g, frontier);
+              : bicgstab_graph<float>(p, B, di, o, rhs, x, cs, g, frontier, epi, epi_done);
   }
   const double* B = system == 0 ? p->Bst.p : p->Bcn.p;
   const double* di = system == 0 ? p->dinv_st.p : p->dinv_cn.p;
   return gm ? gmres_graph<double>(p, B, di, o, rhs, x, cs, g, frontier)
-            : bicgstab_graph<double>(p, B, di, o, rhs, x, cs, g, frontier);
+            : bicgstab_graph<double>(p, B, di, o, rhs, x, cs, g, frontier, epi, epi_done);
 }
 
 const double* krylov_scalars(afc_problem_s* p) { return p->kw ? p->kw->sc.p : nullptr; }
@@ -1302,7 +1321,8 @@ int krylov_cycles_slot() { return S_CYCLES; }
 const void* krylov_key(afc_problem_s* p) { return p->kw ? (const void*)p->kw->vec.base : nullptr; }
 
 int krylov_solve(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, int* its,
-                 double* res) {
+                 double* res, const KrylovEpilogue* epi, bool* epi_done) {
+  if (epi_done) *epi_done = false;
   const bool mixed = o->precision == AFC_MIXED;
   if (mixed && p->precision != AFC_MIXED) {
     set_error("mixed-precision solve needs afc_assemble(..., AFC_MIXED)");
@@ -1313,11 +1333,13 @@ int krylov_solve(afc_problem_s* p, int system, const afc_opts* o, const double* 
   if (mixed) {
     const float* B = system == 0 ? p->Bst32.p : p->Bcn32.p;
     const float* di = system == 0 ? p->dinv_st32.p : p->dinv_cn32.p;
-    return gm ? gmres_impl<float>(p, B, di, o, rhs, x, its, res) : bicgstab_impl<float>(p, B, di, o, rhs, x, its, res);
+    return gm ? gmres_impl<float>(p, B, di, o, rhs, x, its, res)
+              : bicgstab_impl<float>(p, B, di, o, rhs, x, its, res, epi, epi_done);
   }
   const double* B = system == 0 ? p->Bst.p : p->Bcn.p;
   const double* di = system == 0 ? p->dinv_st.p : p->dinv_cn.p;
-  return gm ? gmres_impl<double>(p, B, di, o, rhs, x, its, res) : bicgstab_impl<double>(p, B, di, o, rhs, x, its, res);
+  return gm ? gmres_impl<double>(p, B, di, o, rhs, x, its, res)
+            : bicgstab_impl<double>(p, B, di, o, rhs, x, its, res, epi, epi_done);
 }
 
 }  // namespace afc
