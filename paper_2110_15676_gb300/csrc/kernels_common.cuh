@@ -62,69 +62,18 @@ __device__ __forceinline__ double widen_exact(float x) {
   return __longlong_as_double((long long)bits);
 }
 
-// Sums of the positive and of the negative values among n doubles (given as bit
-// patterns, 0 for absent entries), exact: every mantissa is placed in a 128-bit fixed
-// point scaled to the largest exponent (its mantissa at bits 64..116, so up to 2^10
-// terms cannot overflow), the words are added with carry on the integer pipe, and
-// each total is rounded to double once.  Subnormal inputs count as zero.  On GB300
-// this replaces two FP64 adds per value (an FP64 warp instruction occupies the pipe
-// for 16 cycles) with about a dozen integer instructions, and is more accurate.
-template <int KA>
-__device__ __forceinline__ void exact_signed_sums(const unsigned long long (&bits)[KA], int n, double& pos,
-                                                  double& neg) {
-  unsigned emax = 0;
-#pragma unroll
-  for (int k = 0; k < KA; ++k) {
-    if (k >= n) break;
-    const unsigned e = (unsigned)(bits[k] >> 52) & 0x7ffu;
-    emax = e > emax ? e : emax;
-  }
-  pos = 0.0;
-  neg = 0.0;
-  if (emax == 0u) return;
-  unsigned long long ph = 0, pl = 0, nh = 0, nl = 0;
-#pragma unroll
-  for (int k = 0; k < KA; ++k) {
-    if (k >= n) break;
-    const unsigned long long b = bits[k];
-    const int e = (int)((b >> 52) & 0x7ffu);
-    if (e == 0) continue;
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    const int sh = e - (int)emax + 64;
-    unsigned long long lo, hi;
-    if (sh >= 64) {
-      lo = 0ull;
-      hi = m;
-    } else if (sh > 0) {
-      lo = m << sh;
-      hi = m >> (64 - sh);
-    } else if (sh > -64) {
-      lo = m >> (-sh);
-      hi = 0ull;
-    } else {
-      lo = 0ull;
-      hi = 0ull;
-    }
-    if (b >> 63) {
-      nl += lo;
-      nh += hi + (nl < lo ? 1ull : 0ull);
-    } else {
-      pl += lo;
-      ph += hi + (pl < lo ? 1ull : 0ull);
-    }
-  }
-  const double two64 = 18446744073709551616.0;
-  const int ex = (int)emax - 1139;   // value = fixed point * 2^(emax - 1023 - 52 - 64)
-  pos = scalbn(fma(__ull2double_rn(ph), two64, __ull2double_rn(pl)), ex);
-  neg = -scalbn(fma(__ull2double_rn(nh), two64, __ull2double_rn(nl)), ex);
-}
-
-// The same sums, taken one value at a time so that no value has to be kept: the
-// totals are held in 128-bit fixed point scaled to the largest exponent seen so far,
-// and a value with a larger exponent first shifts both totals right (the bits that
-// leave the 128-bit range are below 2^-64 of the new largest value's last bit).
-// Values only move in and out of registers once, which keeps a row of 26 pair
-// fluxes from holding 52 registers until its largest exponent is known.
+// Sums of the positive and of the negative values of a row's pair fluxes, exact:
+// every mantissa is placed in a 128-bit fixed point scaled to the largest exponent
+// (its mantissa at bits 64..116, so up to 2^10 terms cannot overflow), the words are
+// added with carry on the integer pipe, and each total is rounded to double once.
+// Subnormal inputs count as zero.  On GB300 this replaces two FP64 adds per value (an
+// FP64 warp instruction occupies the pipe for 16 cycles) with about a dozen integer
+// instructions, and is more accurate.  The values are taken one at a time, so that
+// none has to be kept: the totals are held scaled to the largest exponent seen so
+// far, and a value with a larger exponent first shifts both totals right (the bits
+// that leave the 128-bit range are below 2^-64 of the new largest value's last
+// bit).  A row of 26 pair fluxes then needs no 52 registers to hold its bit
+// patterns until its largest exponent is known.
 struct SignedFixedSums {
   unsigned emax = 0u;
   unsigned long long ph = 0ull, pl = 0ull, nh = 0ull, nl = 0ull;
@@ -192,18 +141,21 @@ struct SignedFixedSums {
 __device__ __forceinline__ double imin_nn(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
 }
-// exact 0.5 * x and 2 * x by moving the exponent (normal numbers); FP64 fallback otherwise
+// Exact 0.5 * x (IEEE, ties to even) on the integer pipe.  Normal numbers above the
+// smallest binade move their exponent; zeros, subnormals and the smallest binade
+// halve the 53-bit significand with round-half-even; Inf and NaN pass through.  No
+// branch issues an FP64 instruction, so none costs the FP64 pipe even when the
+// compiler evaluates both sides of a branch.
 __device__ __forceinline__ double half_exact(double x) {
   const long long b = __double_as_longlong(x);
   const long long e = (b >> 52) & 0x7ff;
   if (e > 1 && e < 0x7ff) return __longlong_as_double(b - (1LL << 52));
-  return 0.5 * x;
-}
-__device__ __forceinline__ double twice_exact(double x) {
-  const long long b = __double_as_longlong(x);
-  const long long e = (b >> 52) & 0x7ff;
-  if (e > 0 && e < 0x7fe) return __longlong_as_double(b + (1LL << 52));
-  return x + x;
+  if (e == 0x7ff) return x;
+  const long long sign = b & (long long)0x8000000000000000ULL;
+  const unsigned long long M = (unsigned long long)(b & 0x000FFFFFFFFFFFFFLL) | (e == 1 ? (1ULL << 52) : 0ULL);
+  unsigned long long h = M >> 1;
+  if ((M & 1ULL) && (h & 1ULL)) ++h;   // exactly half-way: to even (may carry into the exponent)
+  return __longlong_as_double(sign | (long long)h);
 }
 
 // R = min{1, num / den} of Zalesak's step 3 for num = m_i Q, den = dt P of the same sign,
