@@ -15,12 +15,17 @@
 // blocks, against 2.6 us for a count that the last block resets before it bumps a
 // separate generation word (two more serial atomics on the release path).
 //
-// Memory: the block's threads meet at __syncthreads, then its first thread fences
-// (cumulatively for the block's writes), arrives, waits and fences again before the
-// block's threads meet once more, so plain loads after the barrier see what other
-// blocks wrote before it.  Arrays
+// Memory: the block's threads meet at __syncthreads, then its first thread issues an
+// acquire-release fence at GPU scope (cumulative over the writes the block made before
+// the meeting) and arrives with a relaxed atomic add; the waiting thread reads the
+// counter with acquire loads, and the block's threads meet once more, so plain loads
+// after the barrier see what other blocks wrote before it.  The acquire-release fence
+// is lighter than the sequentially consistent one of __threadfence().  Arrays
 // written inside a persistent launch must not be read through the read-only
 // (non-coherent) path, i.e. not through const __restrict__ pointers.
+//
+// grid_arrive / grid_wait split the barrier for a block that has work which no other
+// block needs before the barrier: it arrives, does that work, then waits.
 #pragma once
 
 #include "afc_internal.h"
@@ -42,17 +47,32 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ void grid_barrier(GridBar* gb) {
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrive (after the block's threads have met): returns, in thread 0, the counter value
+// before this block's add.
+__device__ __forceinline__ unsigned int grid_arrive(GridBar* gb) {
   __syncthreads();
+  unsigned int old = 0u;
   if (threadIdx.x == 0) {
-    volatile unsigned int* va = &gb->arrive;
-    volatile int* verr = &gb->err;
     const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    __threadfence();
-    const unsigned int old = atomicAdd(&gb->arrive, add);
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    old = atomicAdd(&gb->arrive, add);
+  }
+  return old;
+}
+
+// Wait until every block has arrived (thread 0 passes what grid_arrive returned).
+__device__ __forceinline__ void grid_wait(GridBar* gb, unsigned int old) {
+  if (threadIdx.x == 0) {
+    volatile int* verr = &gb->err;
     if (*verr == 0) {
       const unsigned long long t0 = global_ns();
-      while (((old ^ *va) & 0x80000000u) == 0u) {
+      while (((old ^ ld_acquire_gpu(&gb->arrive)) & 0x80000000u) == 0u) {
         if (*verr != 0) break;
         if (global_ns() - t0 > kBarrierWaitNs) {
           atomicExch(&gb->err, 1);
@@ -60,9 +80,10 @@ __device__ __forceinline__ void grid_barrier(GridBar* gb) {
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
+
+__device__ __forceinline__ void grid_barrier(GridBar* gb) { grid_wait(gb, grid_arrive(gb)); }
 
 }  // namespace afc

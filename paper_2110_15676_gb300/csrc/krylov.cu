@@ -469,12 +469,12 @@ constexpr int kFusedBlocksPerSM = 1;
 // once, and the only block-wide meeting after the barrier is the one that hands
 // the totals on (the totals alternate between two shared slots, like the partials,
 // so a later call cannot overwrite a slot that a thread still reads).
+// grid_sums_begin stores the partials and arrives; grid_sums_end waits and sums, so
+// that work no other block needs can run in between.
 template <int NV>
-__device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& buf, GridBar* bar,
-                                          double (&tot)[NV]) {
+__device__ __forceinline__ unsigned int grid_sums_begin(double (&v)[NV], double* part, int buf, GridBar* bar) {
   static_assert(NV >= 1 && NV <= 2, "two partial buffers of 2 G values");
   __shared__ double col[NV][kFusedBlock];
-  __shared__ double shtot[2][NV];
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* pb = part + (size_t)buf * 2 * G;
@@ -487,7 +487,17 @@ __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& bu
     t = warp_sum(t);
     if (lane == 0) pb[w * G + blockIdx.x] = t;
   }
-  grid_barrier(bar);   // begins with __syncthreads: col is free again after it
+  return grid_arrive(bar);   // begins with __syncthreads: col is free again after it
+}
+
+template <int NV>
+__device__ __forceinline__ void grid_sums_end(double* part, int& buf, GridBar* bar, unsigned int old,
+                                              double (&tot)[NV]) {
+  __shared__ double shtot[2][NV];
+  const int G = gridDim.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* pb = part + (size_t)buf * 2 * G;
+  grid_wait(bar, old);
   if (w < NV) {
     double t = 0.0;
 #pragma unroll 4
@@ -499,6 +509,13 @@ __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& bu
 #pragma unroll
   for (int q = 0; q < NV; ++q) tot[q] = shtot[buf][q];
   buf ^= 1;
+}
+
+template <int NV>
+__device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& buf, GridBar* bar,
+                                          double (&tot)[NV]) {
+  const unsigned int old = grid_sums_begin<NV>(v, part, buf, bar);
+  grid_sums_end<NV>(part, buf, bar, old, tot);
 }
 
 template <int KT, class T>
@@ -590,12 +607,12 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     grid_sums<2>(a2, part, buf, bar, t2);
     omega = t2[0] / t2[1];
     if (!isfinite(omega) || t2[1] == 0.0 || *berr) { done = 2; break; }
-    // x += alpha phat + omega shat, r = s - omega t, ||r||, (rhat, r)
+    // r = s - omega t, ||r||, (rhat, r); x += alpha phat + omega shat while the sums
+    // complete (no other block reads x)
     const T tom = (T)omega;
     b0 = 0;
     b1 = 0;
     for (int64_t i = i0; i < iend; i += stride) {
-      x[i] = x[i] + ta * ph[i] + tom * sh[i];
       const T ri = s[i] - tom * t[i];
       r[i] = ri;
       b0 = fma(ri, ri, b0);
@@ -603,7 +620,9 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     }
     a2[0] = (double)b0;
     a2[1] = (double)b1;
-    grid_sums<2>(a2, part, buf, bar, t2);
+    const unsigned int arrived = grid_sums_begin<2>(a2, part, buf, bar);
+    for (int64_t i = i0; i < iend; i += stride) x[i] = x[i] + ta * ph[i] + tom * sh[i];
+    grid_sums_end<2>(part, buf, bar, arrived, t2);
     nres = sqrt(t2[0]);
     const double rho_old = rho;
     rho = t2[1];
