@@ -124,16 +124,49 @@ struct SignedFixedSums {
       ph += hi + (pl < lo ? 1ull : 0ull);
     }
   }
+  // The totals rounded to double (nearest, ties to even) on the integer pipe; value
+  // = (h:l) * 2^(emax - 1139).  Totals whose double would be subnormal or overflow
+  // take the FP64 route in a separate function.
   __device__ __forceinline__ void result(double& pos, double& neg) const {
     if (emax == 0u) {
       pos = 0.0;
       neg = 0.0;
       return;
     }
-    const double two64 = 18446744073709551616.0;
     const int ex = (int)emax - 1139;
-    pos = scalbn(fma(__ull2double_rn(ph), two64, __ull2double_rn(pl)), ex);
-    neg = -scalbn(fma(__ull2double_rn(nh), two64, __ull2double_rn(nl)), ex);
+    pos = to_double(ph, pl, ex);
+    neg = neg_bits(to_double(nh, nl, ex));
+  }
+  __device__ static __noinline__ double to_double_fp64(unsigned long long h, unsigned long long l, int ex) {
+    const double two64 = 18446744073709551616.0;
+    return scalbn(fma(__ull2double_rn(h), two64, __ull2double_rn(l)), ex);
+  }
+  __device__ static __forceinline__ double to_double(unsigned long long h, unsigned long long l, int ex) {
+    if ((h | l) == 0ull) return 0.0;
+    const int lz = h != 0ull ? __clzll((long long)h) : 64 + __clzll((long long)l);
+    unsigned long long nh, nl;   // normalised: bit 127 set
+    if (lz >= 64) {
+      nh = l << (lz - 64);
+      nl = 0ull;
+    } else if (lz > 0) {
+      nh = (h << lz) | (l >> (64 - lz));
+      nl = l << lz;
+    } else {
+      nh = h;
+      nl = l;
+    }
+    unsigned long long m = nh >> 11;   // 53 bits, the leading one at bit 52
+    const bool half = (nh >> 10) & 1ull;
+    const bool sticky = ((nh & 0x3FFull) | nl) != 0ull;
+    if (half && (sticky || (m & 1ull))) ++m;
+    int e2 = 127 + ex - lz;            // exponent of the leading bit
+    if (m >> 53) {
+      m >>= 1;
+      ++e2;
+    }
+    const int be = e2 + 1023;
+    if (be <= 0 || be >= 2047) return to_double_fp64(h, l, ex);
+    return __longlong_as_double((long long)(((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
   }
 };
 
