@@ -183,7 +183,7 @@ SspArrays ssp_arrays(afc_problem_s* p);
 // The residual functions below store ||res||^2 at *normsq_slot; with a null slot they
 // leave the grid_for(N) block partials of res^2 in p->part for the caller to sum.
 // CN helpers
-int cn_predictor(afc_problem_s* p, const double* u_old, double dt);               // ut, b0, Qp, Qm
+int cn_predictor(afc_problem_s* p, const double* u_old, double dt);   // ut, b0, Qp = m Q+, Qm = m Q-
 int cn_linear_guess(afc_problem_s* p, const double* u_old, double* u);             // u = 2 ut - u_old (after cn_predictor)
 // CN with the MC limiter (Sec. 2.2): Fold = F*(u_old), then res = b0 + (F*(u) + Fold)/2 - (M_L/dt + AA/2) u
 int mc_cn_old_flux(afc_problem_s* p, const double* u_old);

@@ -70,10 +70,12 @@ __global__ void k_cn_predictor(int64_t N, Offsets of, const double* __restrict__
   b0[i] = (m / dt * uo[i] - 0.5 * y) + f[i];
 }
 
-// Q+/- of the CN predictor over N_i (fixed for the whole step).
+// m_i Q+/- of the CN predictor over N_i (fixed for the whole step, so the product
+// with the lumped mass is formed once per step rather than in every factors pass).
 template <int KT>
 __global__ void k_bounds_of(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
-                            const double* __restrict__ v, double* __restrict__ Qp, double* __restrict__ Qm) {
+                            const double* __restrict__ v, const double* __restrict__ mL, double* __restrict__ Qp,
+                            double* __restrict__ Qm) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -87,8 +89,9 @@ __global__ void k_bounds_of(int64_t N, Offsets of, const unsigned long long* __r
     kmax = kj > kmax ? kj : kmax;
     kmin = kj < kmin ? kj : kmin;
   }
-  Qp[i] = from_key(kmax) - vi;
-  Qm[i] = from_key(kmin) - vi;
+  const double m = mL[i];
+  Qp[i] = m * (from_key(kmax) - vi);
+  Qm[i] = m * (from_key(kmin) - vi);
 }
 
 // Node sums of the CN flux: a = u - u_old, s = u + u_old; optionally first
@@ -130,8 +133,8 @@ __global__ void k_cn_edges(int64_t N, Offsets of, const double* __restrict__ mdt
 // Zalesak steps 1-3 for the CN fluxes (Q+/- precomputed from the predictor).
 template <int KT>
 __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
-                             const double* __restrict__ r_up, const double* __restrict__ Qp,
-                             const double* __restrict__ Qm, const double* __restrict__ mL,
+                             const double* __restrict__ r_up, const double* __restrict__ mQp,
+                             const double* __restrict__ mQm,
                              const uint8_t* __restrict__ dir, double dt, double* __restrict__ Rp,
                              double* __restrict__ Rm) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
@@ -148,9 +151,8 @@ __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __
   }
   double Pp, Pm;
   acc.result(Pp, Pm);
-  const double m = mL[i];
-  Rp[i] = zalesak_factor(m * Qp[i], dt * Pp);
-  Rm[i] = zalesak_factor(m * Qm[i], dt * Pm);
+  Rp[i] = zalesak_factor(mQp[i], dt * Pp);
+  Rm[i] = zalesak_factor(mQm[i], dt * Pm);
 }
 
 // Zalesak step 4, F*, and the nonlinear residual of Eq. CNZal:
@@ -308,7 +310,8 @@ int cn_predictor(afc_problem_s* p, const double* u_old, double dt) {
                                                                              p->mL.p, p->dir.p, p->udir.p, dt, p->ut.p,
                                                                              p->b0.p));
     AFC_LAUNCH(p, "k_bounds_of",
-               k_bounds_of<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->ut.p, p->Qp.p, p->Qm.p));
+               k_bounds_of<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->ut.p, p->mL.p, p->Qp.p,
+                                                    p->Qm.p));
   });
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
@@ -424,7 +427,7 @@ int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int li
                                                                        p->cn_s.p, prelimit, p->r_up.p));
     if (limiter == AFC_LIM_ZALESAK)
       AFC_LAUNCH(p, "k_cn_factors", k_cn_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->Qp.p,
-                                                                           p->Qm.p, p->mL.p, p->dir.p, dt, p->Rp.p,
+                                                                           p->Qm.p, p->dir.p, dt, p->Rp.p,
                                                                            p->Rm.p));
     AFC_LAUNCH(p, "k_cn_residual",
                k_cn_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->r_up.p, p->AA.p, u_new,
