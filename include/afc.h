@@ -413,6 +413,20 @@ int afc_profile(afc_problem p, int mode);
 int afc_profile_read(afc_problem p, int cap, char* names, double* total_ms, int64_t* launches, int* n,
                      int64_t* all_launches);
 
+/* Self-test of the bounded grid waits of the persistent kernels (their failure
+ * detection, exercised without a fault).  One launch of two blocks on `device`
+ * in which block 1 never arrives at a grid barrier, so block 0's wait runs out
+ * after limit_ms milliseconds of the device's global timer (0 < limit_ms <=
+ * 4000), records the error in the barrier state and returns, as a barrier of a
+ * solver launch does after its 4 s limit.  *observed receives the status the
+ * host derives from that state (AFC_E_TIMEOUT when the wait ran out, AFC_OK if
+ * it did not), *waited_ms (may be NULL) the host-measured duration of the launch.
+ * Returns AFC_OK when a launch after the expired wait ran and returned its
+ * result (the context stays usable), AFC_E_INVALID for a bad limit or a NULL
+ * `observed`, AFC_E_CUDA on a CUDA error.  Allocates and frees 20 bytes of
+ * device memory. */
+int afc_selftest_grid_wait(int device, double limit_ms, int* observed, double* waited_ms);
+
 const char* afc_status_str(int status);
 const char* afc_last_error(void);
 

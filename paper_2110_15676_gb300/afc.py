@@ -136,6 +136,7 @@ _SIGS = {
     "afc_serve_release": (C.c_int, [_P, C.c_int64]),
     "afc_serve_get_info": (C.c_int, [_P, C.POINTER(afc_serve_info)]),
     "afc_serve_destroy": (C.c_int, [_P]),
+    "afc_selftest_grid_wait": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_int), _D]),
     "afc_status_str": (C.c_char_p, [C.c_int]),
     "afc_last_error": (C.c_char_p, []),
 }
@@ -171,6 +172,15 @@ def _f64(a, n=None) -> np.ndarray:
     if n is not None and a.size != n:
         raise ValueError(f"expected {n} values, got {a.size}")
     return a
+
+
+def selftest_grid_wait(limit_ms: float = 50.0, device: int = 0) -> tuple[int, float]:
+    """Run afc_selftest_grid_wait: (status the expired barrier reports, launch ms)."""
+    obs = C.c_int(-1)
+    ms = C.c_double(0.0)
+    _check(_lib.afc_selftest_grid_wait(int(device), float(limit_ms), C.byref(obs), C.byref(ms)),
+           "afc_selftest_grid_wait")
+    return obs.value, ms.value
 
 
 def default_opts(**kw) -> afc_opts:

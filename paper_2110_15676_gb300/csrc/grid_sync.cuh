@@ -66,15 +66,17 @@ __device__ __forceinline__ unsigned int grid_arrive(GridBar* gb) {
   return old;
 }
 
-// Wait until every block has arrived (thread 0 passes what grid_arrive returned).
-__device__ __forceinline__ void grid_wait(GridBar* gb, unsigned int old) {
+// Wait until every block has arrived (thread 0 passes what grid_arrive returned);
+// give up after limit_ns of the global timer.
+__device__ __forceinline__ void grid_wait(GridBar* gb, unsigned int old,
+                                          unsigned long long limit_ns = kBarrierWaitNs) {
   if (threadIdx.x == 0) {
     volatile int* verr = &gb->err;
     if (*verr == 0) {
       const unsigned long long t0 = global_ns();
       while (((old ^ ld_acquire_gpu(&gb->arrive)) & 0x80000000u) == 0u) {
         if (*verr != 0) break;
-        if (global_ns() - t0 > kBarrierWaitNs) {
+        if (global_ns() - t0 > limit_ns) {
           atomicExch(&gb->err, 1);
           break;
         }

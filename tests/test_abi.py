@@ -58,3 +58,12 @@ def test_invalid_meshes_rejected_on_host():
     with pytest.raises(afc.AfcError) as e:
         afc.Problem.from_elements("p1", rng.uniform(size=(n, 3)), conn)
     assert "offsets" in str(e.value)
+
+
+def test_grid_wait_selftest_rejects_bad_limits_on_host():
+    from paper_2110_15676_gb300 import afc
+    obs = C.c_int(-1)
+    for bad in (0.0, -1.0, 4001.0, float("nan")):
+        assert afc.afc_selftest_grid_wait(0, bad, C.byref(obs), None) == afc.AFC_E_INVALID
+    assert afc.afc_selftest_grid_wait(0, 10.0, None, None) == afc.AFC_E_INVALID
+    assert obs.value == -1
