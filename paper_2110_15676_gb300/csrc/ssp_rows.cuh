@@ -23,7 +23,7 @@ namespace afc {
 
 // Flux of the pair (i, i + o_k) seen from row i, stored once per pair as a float.
 __device__ __forceinline__ double pair_flux32(const Offsets& of, int Kup, int k, int64_t i, int64_t N,
-                                              const float* __restrict__ r32) {
+                                              const float* r32) {
   if (k > Kup) return widen_exact(r32[(int64_t)(k - Kup - 1) * N + i]);
   return neg_bits(widen_exact(r32[(int64_t)(Kup - 1 - k) * N + i + of.o[k]]));
 }
