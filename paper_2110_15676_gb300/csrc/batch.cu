@@ -271,8 +271,12 @@ int build_table(afc_batch_s* b, int block, const double* dt, double dt_all, bool
   for (size_t q = 0; q < n; ++q) dts[q] = dt ? dt[q] : dt_all;
   if (mixed)
     for (auto* p : b->list) {
+      // the single-precision copies are made on the instance's own stream: wait for
+      // them there before the batch's stream reads them
+      const bool ready = p->ssp32_ready;
       int st = ensure_ssp_mixed(p);   // no-op once the copies match the assembly
       if (st) return st;
+      if (!ready && p->stream != b->stream) AFC_CUDA(cudaStreamSynchronize(p->stream));
     }
   if (b->tab_block == block && b->tab_dt == dts) return AFC_OK;
   // the previous upload may still be reading the pinned table

@@ -50,3 +50,46 @@ def test_persistent_batched_mixed_equals_solo(mode_name):
                 assert np.array_equal(u, solo[q]), (mode_name, blk, q, float(np.abs(u - solo[q]).max()))
     for g in gs:
         g.close()
+
+
+def test_batched_mixed_instances_on_their_own_streams_equal_solo():
+    """Instances created on their own streams, batched on the first one's stream while
+    other work keeps the GPU busy on a third stream: the single-precision copies that
+    the first mixed batched step makes are enqueued on each instance's stream, and the
+    batch's stream must not read them before they are done."""
+    import torch
+    from paper_2110_15676_gb300 import afc
+    rng = np.random.default_rng(91)
+    wls = [W.random_transient(rng, elem, (n, n)) for elem, n in (("q1", 41), ("q1", 81), ("p1", 64))]
+    steps = 4
+    solo, dts = [], []
+    for wl in wls:
+        g = _gpu(wl, "mixed")
+        dt = g.cfl_timestep(0.5)
+        dts.append(dt)
+        o = afc.default_opts(scheme=afc.AFC_SSP3, dt=dt, precision=afc.AFC_MIXED)
+        for _ in range(steps):
+            g.step(o)
+        solo.append(g.get_solution())
+        g.close()
+    opts = afc.default_opts(scheme=afc.AFC_SSP3, precision=afc.AFC_MIXED)
+    busy = torch.cuda.Stream()
+    a = torch.randn(4096, 4096, device="cuda")
+    for trial in range(3):
+        streams = [torch.cuda.Stream() for _ in wls]
+        gs = []
+        for wl, st in zip(wls, streams):
+            with torch.cuda.stream(st):
+                gs.append(_gpu(wl, "mixed"))
+        with torch.cuda.stream(busy):
+            for _ in range(40):
+                a = torch.tanh(a @ a * 1e-3)
+        with afc.Batch(gs) as b:
+            b.set_tuning(afc.AFC_BATCH_PER_STAGE, 256)
+            b.step(opts, dt=dts, nsteps=steps)
+            for q, g in enumerate(gs):
+                u = g.get_solution()
+                assert np.array_equal(u, solo[q]), (trial, q, float(np.abs(u - solo[q]).max()))
+        for g in gs:
+            g.close()
+    torch.cuda.synchronize()
