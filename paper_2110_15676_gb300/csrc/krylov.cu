@@ -531,15 +531,19 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
   volatile int* berr = &bar->err;
   int buf = 0;
   double a1[1], t1[1], a2[2], t2[2];
-  // r = rhs, rhat = r, x = p = v = 0, rho = (r, r)
+  // r = rhs, rhat = r, x = v = 0, rho = (r, r); and the first iteration's p update
+  // (beta = 0 and p = v = 0 before it: p = r + 0, phat = D^{-1} p), so that
+  // iteration needs no pass and no barrier of its own before its product
   T a0 = 0;
   for (int64_t i = i0; i < iend; i += stride) {
     const T ri = (T)rhs[i];
     x[i] = 0;
     r[i] = ri;
     rh[i] = ri;
-    pv[i] = 0;
     v[i] = 0;
+    const T pi = ri + (T)0;   // as r + 0 * (0 - 1 * 0) rounds: -0 becomes +0
+    pv[i] = pi;
+    ph[i] = dinv[i] * pi;
     a0 = fma(ri, ri, a0);
   }
   a1[0] = (double)a0;
@@ -550,15 +554,19 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
   double alpha = 1.0, omega = 1.0, beta = 0.0, nres = n0;
   int its = 0;
   int done = !isfinite(n0) ? 2 : (n0 < tol ? 1 : (maxit <= 0 ? 4 : 0));
+  bool first = true;
   while (done == 0) {
-    // p = r + beta (p - omega v), phat = D^{-1} p
-    const T tb = (T)beta, to = (T)omega;
-    for (int64_t i = i0; i < iend; i += stride) {
-      const T pi = r[i] + tb * (pv[i] - to * v[i]);
-      pv[i] = pi;
-      ph[i] = dinv[i] * pi;
+    // p = r + beta (p - omega v), phat = D^{-1} p (the first iteration's came with r)
+    if (!first) {
+      const T tb = (T)beta, to = (T)omega;
+      for (int64_t i = i0; i < iend; i += stride) {
+        const T pi = r[i] + tb * (pv[i] - to * v[i]);
+        pv[i] = pi;
+        ph[i] = dinv[i] * pi;
+      }
+      grid_barrier(bar);
     }
-    grid_barrier(bar);
+    first = false;
     // v = B phat, alpha = rho / (rhat, v)
     a0 = 0;
     for (int64_t i = i0; i < iend; i += stride) {
