@@ -1,10 +1,12 @@
 """Brute force on meshes of one to two cells: the oracle's vectorised limiters
 equal the dense loop-by-loop transcriptions of tests/bruteforce.py over every sign
-pattern of the raw fluxes and every Dirichlet mask (Zalesak, one tetrahedron), and
+pattern of the raw fluxes and every Dirichlet mask (Zalesak, one tetrahedron), over
+sampled sign patterns and masks on two tetrahedra and two hexahedra (Zalesak), and
 over every ordering of the nodal values (MC)."""
 import itertools
 
 import numpy as np
+import pytest
 
 from oracle import afc_oracle as O
 import bruteforce as BF
@@ -47,6 +49,48 @@ def test_zalesak_every_sign_pattern_and_dirichlet_mask():
             assert np.abs(F - F_bf).max() <= 1e-15 * max(np.abs(F_bf).max(), 1.0)
             checked += 1
     assert checked == 16 * 729
+
+
+def _zalesak_case(prob, mC, u_tilde, dt, mask, r):
+    I, J = prob.pairs
+    rd = r[I, J]
+    alpha, lim = O.zalesak_limiter(prob, rd, u_tilde, dt, "zalesak")
+    F = O.limited_sum(prob, alpha, rd)
+    a_bf, F_bf, Rp_bf, Rm_bf = BF.zalesak(r, mC, prob.mL, u_tilde, dt, np.asarray(mask, bool))
+    assert np.array_equal(lim["Rp"], Rp_bf) and np.array_equal(lim["Rm"], Rm_bf)
+    nz = rd != 0.0                          # alpha is irrelevant where r = 0 (reading A11)
+    assert np.array_equal(alpha[nz], a_bf[I, J][nz])
+    assert np.abs(F - F_bf).max() <= 1e-15 * max(np.abs(F_bf).max(), 1.0)
+
+
+@pytest.mark.parametrize("case,n_masks,n_signs", [("two_tets", 32, 120), ("two_hexes", 10, 60)])
+def test_zalesak_sampled_sign_patterns_on_two_cells(case, n_masks, n_signs):
+    """Sec. 2.1.3, steps 1-4 on two cells sharing a face: every Dirichlet mask of the
+    two tetrahedra (10 seeded masks of the hexahedra) and seeded sign patterns of the
+    raw fluxes, including zero fluxes, so that a node's P+/- and Q+/- collect pairs of
+    both cells."""
+    elem, xyz, conn = getattr(BF, case)()
+    N = len(xyz)
+    rng = np.random.default_rng(5)
+    base = _problem(elem, xyz, conn, np.zeros(N))
+    mC = base.MC.toarray()
+    pairs = [(i, j) for i in range(N) for j in range(i + 1, N) if mC[i, j] != 0.0]
+    dt = O.cfl_timestep(base, 0.5)
+    masks = list(itertools.product([0, 1], repeat=N)) if 2 ** N <= n_masks else \
+        [tuple(rng.integers(0, 2, N)) for _ in range(n_masks)]
+    checked = 0
+    for mask in masks:
+        prob = _problem(elem, xyz, conn, mask)
+        u_tilde = rng.uniform(size=N)
+        for _ in range(n_signs):
+            signs = rng.choice([-1.0, 0.0, 1.0], size=len(pairs), p=[0.45, 0.1, 0.45])
+            r = np.zeros((N, N))
+            for (i, j), sg in zip(pairs, signs):
+                r[i, j] = sg * rng.uniform(0.1, 1.0)
+                r[j, i] = -r[i, j]
+            _zalesak_case(prob, mC, u_tilde, dt, mask, r)
+            checked += 1
+    assert checked == len(masks) * n_signs
 
 
 def test_mc_every_ordering_of_the_nodal_values():

@@ -151,6 +151,29 @@ def test_prelimiting_shrinks_and_keeps_sign():
     assert np.abs(pre[_mate(prob)] + pre).max() <= 1e-15 * np.abs(pre).max()
 
 
+def test_prelimiting_saturates_at_twice_the_diffusive_flux():
+    """Eq. prelimiting with L = 2: where the raw CN flux and the diffusive flux
+    d_ij (ubar_j - ubar_i) at the CN average agree in sign, the prelimited flux is
+    the raw flux itself if it is at most twice the diffusive flux in magnitude, and
+    exactly twice the diffusive flux otherwise.  The diffusive flux is what
+    Eq. flux_002 leaves when the mass term vanishes (dt -> infinity), so it is taken
+    from the oracle's own raw flux at dt = inf, not retyped; an oracle with L = 1
+    (or with the plain u^n instead of the average) fails."""
+    prob, u_old, dt = _cn_problem(seed=5)
+    rng = np.random.default_rng(13)
+    u_new = u_old + rng.normal(scale=0.05, size=u_old.shape)
+    raw = O.cn_fluxes(prob, u_new, u_old, dt, prelimit=False)
+    pre = O.cn_fluxes(prob, u_new, u_old, dt, prelimit=True)
+    diff = O.cn_fluxes(prob, u_new, u_old, np.inf, prelimit=False)
+    same = raw * diff > 0
+    big = same & (np.abs(raw) > 2.0 * np.abs(diff))
+    small = same & (np.abs(raw) < 2.0 * np.abs(diff))
+    assert big.sum() > 50 and small.sum() > 50          # both branches occur
+    assert np.array_equal(pre[big], 2.0 * diff[big])
+    assert np.array_equal(pre[small], raw[small])
+    assert (pre[~same] == 0).all()
+
+
 # ---------------------------------------------------------------- MC
 def _mc_problem(elem="p1", n=9):
     wl = W.stationary_inflow(elem, n)
