@@ -224,8 +224,10 @@ int afc_mc_limited_sum(afc_problem p, int limiter, const double* u, double* umax
  *  Fstar  device array of N doubles, output F*_i (0 at Dirichlet rows).
  * The bounds u_max / u_min it needs live in a fixed 4 MiB device array that
  * every GPU loading the library holds until exit, so N may be at most 262144
- * (AFC_E_INVALID otherwise).  No cudaMalloc, cudaFree or allocating library
- * call is made.  Work is enqueued on the problem's stream and the call returns
+ * (AFC_E_INVALID otherwise).  Like afc_mc_limited_sum it needs the MC family
+ * assembly for any limiter but NONE (AFC_E_STATE otherwise).  The calling
+ * thread's current device is the same after the call as before it.  No
+ * cudaMalloc, cudaFree or allocating library call is made.  Work is enqueued on the problem's stream and the call returns
  * without synchronising.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the array: calls that overlap on the GPU (other
@@ -237,6 +239,11 @@ int afc_mc_limited_sum_noalloc(afc_problem p, int limiter, const double* u, doub
  * `limiter`) and res = f + F*(u) - AA u into internal buffers.  Only enqueued on
  * the problem's stream (no synchronisation, no host copy): for timing the sweep. */
 int afc_mc_residual_sweep(afc_problem p, int limiter);
+
+/* Copy out (host array of N) the nonlinear residual res = f + F*(u) - AA u of the
+ * stationary problem (Sec. 4; 0 at Dirichlet rows) that the last
+ * afc_mc_residual_sweep left in its internal buffer.  Synchronises the stream. */
+int afc_get_residual(afc_problem p, double* res);
 
 /* y = AA x (which = AFC_MAT_LOW) or y = M x (AFC_MAT_MC), host arrays of N. */
 int afc_apply(afc_problem p, int which, const double* x, double* y);
@@ -426,6 +433,17 @@ int afc_profile_read(afc_problem p, int cap, char* names, double* total_ms, int6
  * `observed`, AFC_E_CUDA on a CUDA error.  Allocates and frees 20 bytes of
  * device memory. */
 int afc_selftest_grid_wait(int device, double limit_ms, int* observed, double* waited_ms);
+
+/* Limit of the bounded waits at the grid barriers of this problem's persistent
+ * BiCGStab launches (default 4000 ms, the largest allowed; 0 <= limit_ms <= 4000).
+ * A wait that reaches it records the error and every later barrier of the launch
+ * passes at once, so the launch ends; afc_step / afc_solve_stationary then return
+ * AFC_E_TIMEOUT (the solution is not a valid iterate: restore it with
+ * afc_set_solution) and clear the barrier state for the next call.  With 0 the
+ * first wait that finds a barrier still closed gives up at once, which lets a test
+ * take the timeout path without any fault.  Failure detection of the solver
+ * (bounded device waits), not part of the method. */
+int afc_set_grid_wait_limit(afc_problem p, double limit_ms);
 
 const char* afc_status_str(int status);
 const char* afc_last_error(void);

@@ -114,6 +114,7 @@ _SIGS = {
     "afc_mc_limited_sum": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
     "afc_mc_limited_sum_noalloc": (C.c_int, [_P, C.c_int, _P, _P]),
     "afc_mc_residual_sweep": (C.c_int, [_P, C.c_int]),
+    "afc_get_residual": (C.c_int, [_P, _D]),
     "afc_apply": (C.c_int, [_P, C.c_int, _D, _D]),
     "afc_linear_solve": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(afc_opts), _D, _D, _I32, _D]),
     "afc_profile": (C.c_int, [_P, C.c_int]),
@@ -137,6 +138,7 @@ _SIGS = {
     "afc_serve_get_info": (C.c_int, [_P, C.POINTER(afc_serve_info)]),
     "afc_serve_destroy": (C.c_int, [_P]),
     "afc_selftest_grid_wait": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_int), _D]),
+    "afc_set_grid_wait_limit": (C.c_int, [_P, C.c_double]),
     "afc_status_str": (C.c_char_p, [C.c_int]),
     "afc_last_error": (C.c_char_p, []),
 }
@@ -150,11 +152,32 @@ EXPORTED = tuple(_SIGS)
 
 
 class AfcError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, detail: str | None = None):
         msg = _lib.afc_status_str(status).decode()
-        detail = _lib.afc_last_error().decode()
+        if detail is None:
+            detail = _lib.afc_last_error().decode()
         super().__init__(f"{where}: {msg} ({status}): {detail}")
         self.status = status
+
+
+def check_device_vector(t, n: int, device: int, name: str, where: str):
+    """Reject, before any library call, a tensor that a device-pointer entry point
+    cannot take: it must be a contiguous CUDA float64 tensor of exactly n elements
+    on `device`.  Raises AfcError(AFC_E_INVALID)."""
+    def bad(why):
+        raise AfcError(AFC_E_INVALID, where, f"{name} {why}")
+    if not (hasattr(t, "data_ptr") and hasattr(t, "is_cuda")):
+        bad("is not a tensor")
+    if not t.is_cuda:
+        bad("is not on a CUDA device")
+    if str(t.dtype) != "torch.float64":
+        bad(f"has dtype {t.dtype}, not torch.float64")
+    if not t.is_contiguous():
+        bad("is not contiguous")
+    if t.numel() != n:
+        bad(f"has {t.numel()} elements, not {n}")
+    if t.device.index is not None and t.device.index != device:
+        bad(f"is on cuda:{t.device.index}, the problem on cuda:{device}")
 
 
 def _check(st: int, where: str, allow_not_converged=False) -> int:
@@ -211,9 +234,10 @@ def current_stream_handle():
 class Problem:
     """Owner of one afc_problem handle."""
 
-    def __init__(self, handle: C.c_void_p, n_nodes: int):
+    def __init__(self, handle: C.c_void_p, n_nodes: int, device: int = 0):
         self.h = handle
         self.N = int(n_nodes)
+        self.device = int(device)
 
     @classmethod
     def structured(cls, elem, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), device=0, stream=None):
@@ -225,7 +249,7 @@ class Problem:
                                         device, stream if stream is not None else current_stream_handle(),
                                         C.byref(h))
         _check(st, "afc_create_structured")
-        return cls(h, int(np.prod(n)))
+        return cls(h, int(np.prod(n)), device)
 
     @classmethod
     def from_elements(cls, elem, xyz, conn, device=0, stream=None):
@@ -237,7 +261,7 @@ class Problem:
                                            conn.ctypes.data_as(_I32), device,
                                            stream if stream is not None else current_stream_handle(), C.byref(h))
         _check(st, "afc_create_from_elements")
-        return cls(h, xyz.size // 3)
+        return cls(h, xyz.size // 3, device)
 
     def close(self):
         if self.h:
@@ -347,10 +371,23 @@ class Problem:
         return out
 
     def mc_limited_sum_noalloc(self, u, Fstar, limiter=AFC_LIM_MC):
-        """Device-pointer variant that allocates nothing (u, Fstar: CUDA float64 tensors of N)."""
+        """Device-pointer variant that allocates nothing (u, Fstar: contiguous CUDA
+        float64 tensors of N elements on the problem's device, checked here)."""
+        check_device_vector(u, self.N, self.device, "u", "afc_mc_limited_sum_noalloc")
+        check_device_vector(Fstar, self.N, self.device, "Fstar", "afc_mc_limited_sum_noalloc")
         _check(_lib.afc_mc_limited_sum_noalloc(self.h, limiter, C.c_void_p(u.data_ptr()),
                                                C.c_void_p(Fstar.data_ptr())), "afc_mc_limited_sum_noalloc")
         return Fstar
+
+    def get_residual(self) -> np.ndarray:
+        """The residual f + F*(u) - AA u that the last mc_residual_sweep left (host copy)."""
+        r = np.zeros(self.N)
+        _check(_lib.afc_get_residual(self.h, _dp(r)), "afc_get_residual")
+        return r
+
+    def set_grid_wait_limit(self, limit_ms: float):
+        """Bounded-wait limit (ms) of the grid barriers of this problem's persistent solver launches."""
+        _check(_lib.afc_set_grid_wait_limit(self.h, float(limit_ms)), "afc_set_grid_wait_limit")
 
     def mc_residual_sweep(self, limiter=AFC_LIM_MC):
         """Enqueue one MC limiter + residual sweep on the stored solution (no sync)."""

@@ -164,6 +164,8 @@ struct afc_problem_s {
   afc::StepGraph* g_stat = nullptr;   // cached graph of afc_solve_stationary
   cudaStream_t cap_stream = nullptr;  // private stream used to capture graphs
   int64_t launches = 0;             // kernel launches issued on this problem
+  // bounded-wait limit of the grid barriers in this problem's persistent launches
+  unsigned long long grid_wait_ns = 4000000000ull;
   int64_t device_bytes = 0;
 };
 

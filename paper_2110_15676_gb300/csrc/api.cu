@@ -586,6 +586,14 @@ int afc_mc_residual_sweep(afc_problem p, int limiter) {
   return mc_limited_residual(p, p->u.p, limiter, p->res.p, p->scal.p);
 }
 
+int afc_get_residual(afc_problem p, double* res) {
+  int st = check(p, true);
+  if (st) return st;
+  if (!res) { set_error("null argument"); return AFC_E_INVALID; }
+  if ((st = to_host(p, res, p->res.p, p->N))) return st;
+  return sync(p);
+}
+
 int afc_apply(afc_problem p, int which, const double* x, double* y) {
   int st = check(p, true);
   if (st) return st;
@@ -613,6 +621,17 @@ int afc_linear_solve(afc_problem p, int system, double dt, const afc_opts* o, co
   if ((st = to_host(p, x, p->delta.p, p->N))) return st;
   if ((st = sync(p))) return st;
   return status;
+}
+
+int afc_set_grid_wait_limit(afc_problem p, double limit_ms) {
+  int st = check(p, false);
+  if (st) return st;
+  if (!(limit_ms >= 0.0 && limit_ms <= 4000.0)) {
+    set_error("afc_set_grid_wait_limit: need 0 <= limit_ms <= 4000");
+    return AFC_E_INVALID;
+  }
+  p->grid_wait_ns = (unsigned long long)(limit_ms * 1e6);
+  return AFC_OK;
 }
 
 }  // extern "C"

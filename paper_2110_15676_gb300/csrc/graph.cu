@@ -22,9 +22,11 @@ namespace {
 // fixed-point scalar slots (problem scalars p->scal)
 enum : int {
   F_NORMSQ = 0, F_CORR = 1, F_INNER = 2, F_RES0 = 3, F_RESF = 4, F_STATUS = 5, F_THRESH = 6, F_FIXED = 7,
-  F_MAXIT = 8, F_KBODY = 9, F_REVAL = 10
+  F_MAXIT = 8, F_KBODY = 9, F_REVAL = 10, F_TIMEOUT = 11
 };
-// F_STATUS: 0 running, 1 converged / fixed count reached, 2 non-finite, 3 iteration limit
+// F_STATUS: 0 running, 1 converged / fixed count reached, 2 non-finite or a solver that
+// could not finish, 3 iteration limit; F_TIMEOUT: 1 after a grid barrier of the
+// persistent BiCGStab gave up waiting (F_STATUS is then 2)
 
 __global__ void k_fp_init(double* sc, double thresh, int fixed, int maxit) {
   if (threadIdx.x != 0) return;
@@ -36,6 +38,7 @@ __global__ void k_fp_init(double* sc, double thresh, int fixed, int maxit) {
   sc[F_MAXIT] = (double)maxit;
   sc[F_KBODY] = 0.0;
   sc[F_REVAL] = 0.0;
+  sc[F_TIMEOUT] = 0.0;
 }
 
 // After a residual evaluation: R = ||res||; stop or solve.  The residual pass leaves
@@ -77,6 +80,10 @@ __global__ void k_fp_after_solve(double* sc, const double* __restrict__ ksc, int
   sc[F_INNER] += ksc[kKrylovItsSlot];
   sc[F_KBODY] += gmres ? ksc[cycles_slot] : ksc[kKrylovItsSlot];
   if (ksc[kKrylovDoneSlot] == 2.0) sc[F_STATUS] = 2.0;
+  if (!gmres && ksc[kKrylovBarrierErrSlot] != 0.0) {
+    sc[F_STATUS] = 2.0;
+    sc[F_TIMEOUT] = 1.0;
+  }
 }
 
 __global__ void k_copy(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
@@ -164,8 +171,8 @@ std::vector<unsigned char> make_key(afc_problem_s* p, const afc_opts* o, int wha
   double cdt = p->cn_dt;
   uintptr_t cdt_bits;
   std::memcpy(&cdt_bits, &cdt, sizeof(cdt_bits));
-  uintptr_t extra[6] = {(uintptr_t)what, (uintptr_t)p->stream, (uintptr_t)krylov_key(p), (uintptr_t)p->AA.p,
-                        (uintptr_t)p->Bcn.p, cdt_bits};
+  uintptr_t extra[7] = {(uintptr_t)what, (uintptr_t)p->stream, (uintptr_t)krylov_key(p), (uintptr_t)p->AA.p,
+                        (uintptr_t)p->Bcn.p, cdt_bits, (uintptr_t)p->grid_wait_ns};
   std::memcpy(k.data() + sizeof(afc_opts), extra, sizeof(extra));
   return k;
 }
@@ -287,8 +294,17 @@ int run_fixed_point_graph(afc_problem_s* p, StepGraph& sg, afc_stats* stt) {
   const double* h = p->host_scal;
   const int64_t reval = (int64_t)h[F_REVAL], corr = (int64_t)h[F_CORR], kbody = (int64_t)h[F_KBODY];
   p->launches += sg.k_pro + reval * sg.k_outer + corr * sg.k_solve + kbody * sg.k_body + sg.k_epi;
-  const int status = h[F_STATUS] == 1.0 ? AFC_OK : h[F_STATUS] == 2.0 ? AFC_E_NAN : AFC_NOT_CONVERGED;
-  if (status == AFC_E_NAN) set_error("non-finite nonlinear residual or Krylov breakdown");
+  int status = h[F_STATUS] == 1.0 ? AFC_OK : h[F_STATUS] == 2.0 ? AFC_E_NAN : AFC_NOT_CONVERGED;
+  if (h[F_TIMEOUT] != 0.0) {
+    // the barrier counter is inconsistent after blocks skipped barriers: clear it so
+    // that the next persistent launch starts from a clean state
+    const int rs = krylov_reset_barrier(p);
+    if (rs) return rs;
+    status = AFC_E_TIMEOUT;
+    set_error("a grid barrier of the persistent BiCGStab launch gave up waiting");
+  } else if (status == AFC_E_NAN) {
+    set_error("non-finite nonlinear residual or Krylov breakdown");
+  }
   if (stt) {
     stt->outer_its = (int)corr;
     stt->inner_its = (int)h[F_INNER];

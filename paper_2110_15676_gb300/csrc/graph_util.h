@@ -62,6 +62,11 @@ int krylov_graph(afc_problem_s* p, int system, const afc_opts* o, const double* 
 const double* krylov_scalars(afc_problem_s* p);
 constexpr int kKrylovItsSlot = 7;
 constexpr int kKrylovDoneSlot = 8;
+// 1 after a grid barrier of the persistent BiCGStab launch gave up waiting
+constexpr int kKrylovBarrierErrSlot = 19;
 int krylov_cycles_slot();
+// Clear the grid barrier state of the persistent BiCGStab after a timeout (its
+// counter is left inconsistent when blocks skip barriers); synchronises the stream.
+int krylov_reset_barrier(afc_problem_s* p);
 
 }  // namespace afc

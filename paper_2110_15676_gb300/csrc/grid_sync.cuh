@@ -68,7 +68,8 @@ __device__ __forceinline__ unsigned int grid_arrive(GridBar* gb) {
 }
 
 // Wait until every block has arrived (thread 0 passes what grid_arrive returned);
-// give up after limit_ns of the global timer.
+// give up once limit_ns of the global timer have passed (limit 0: at the first poll
+// that finds the barrier still closed).
 __device__ __forceinline__ void grid_wait(GridBar* gb, unsigned int old,
                                           unsigned long long limit_ns = kBarrierWaitNs) {
   if (threadIdx.x == 0) {
@@ -77,7 +78,7 @@ __device__ __forceinline__ void grid_wait(GridBar* gb, unsigned int old,
       const unsigned long long t0 = global_ns();
       while (((old ^ ld_acquire_gpu(&gb->arrive)) & 0x80000000u) == 0u) {
         if (*verr != 0) break;
-        if (global_ns() - t0 > limit_ns) {
+        if (global_ns() - t0 >= limit_ns) {
           atomicExch(&gb->err, 1);
           break;
         }
@@ -87,6 +88,8 @@ __device__ __forceinline__ void grid_wait(GridBar* gb, unsigned int old,
   __syncthreads();
 }
 
-__device__ __forceinline__ void grid_barrier(GridBar* gb) { grid_wait(gb, grid_arrive(gb)); }
+__device__ __forceinline__ void grid_barrier(GridBar* gb, unsigned long long limit_ns = kBarrierWaitNs) {
+  grid_wait(gb, grid_arrive(gb), limit_ns);
+}
 
 }  // namespace afc

@@ -193,8 +193,10 @@ enum : int {
 };
 // S_DONE: 0 running, 1 converged, 2 breakdown / non-finite, 3 converged at s (x update pending), 4 maxit
 static_assert(S_ITS == kKrylovItsSlot && S_DONE == kKrylovDoneSlot, "slot numbers shared with graph.cu");
-constexpr int S_CYCLES = 17;   // GMRES restart cycles begun (true-residual evaluations)
-static_assert(S_CYCLES < S_CS, "slot range");
+constexpr int S_CYCLES = 18;   // GMRES restart cycles begun (true-residual evaluations)
+constexpr int S_BERR = 19;     // persistent BiCGStab: a grid barrier gave up waiting
+static_assert(S_CYCLES > S_NO_REORTH && S_BERR > S_CYCLES && S_BERR < S_CS, "slot range");
+static_assert(S_BERR == kKrylovBarrierErrSlot, "slot number shared with graph.cu");
 
 struct KrylovWork {
   int64_t N = 0;
@@ -492,12 +494,12 @@ __device__ __forceinline__ unsigned int grid_sums_begin(double (&v)[NV], double*
 
 template <int NV>
 __device__ __forceinline__ void grid_sums_end(double* part, int& buf, GridBar* bar, unsigned int old,
-                                              double (&tot)[NV]) {
+                                              double (&tot)[NV], unsigned long long wait_ns) {
   __shared__ double shtot[2][NV];
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double* pb = part + (size_t)buf * 2 * G;
-  grid_wait(bar, old);
+  grid_wait(bar, old, wait_ns);
   if (w < NV) {
     double t = 0.0;
 #pragma unroll 4
@@ -513,9 +515,9 @@ __device__ __forceinline__ void grid_sums_end(double* part, int& buf, GridBar* b
 
 template <int NV>
 __device__ __forceinline__ void grid_sums(double (&v)[NV], double* part, int& buf, GridBar* bar,
-                                          double (&tot)[NV]) {
+                                          double (&tot)[NV], unsigned long long wait_ns) {
   const unsigned int old = grid_sums_begin<NV>(v, part, buf, bar);
-  grid_sums_end<NV>(part, buf, bar, old, tot);
+  grid_sums_end<NV>(part, buf, bar, old, tot, wait_ns);
 }
 
 template <int KT, class T>
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
                                                    const T* __restrict__ dinv, const double* __restrict__ rhs,
                                                    double* xout, T* x, T* r, T* rh, T* pv, T* v, T* s, T* t, T* ph,
                                                    T* sh, double* part, GridBar* bar, double atol, double rtol,
-                                                   int maxit, KrylovEpilogue ep) {
+                                                   int maxit, KrylovEpilogue ep, unsigned long long wait_ns) {
   const int K = KT > 0 ? KT : of.K;
   const int64_t G = gridDim.x;
   const int64_t stride = kFusedBlock;
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     a0 = fma(ri, ri, a0);
   }
   a1[0] = (double)a0;
-  grid_sums<1>(a1, part, buf, bar, t1);
+  grid_sums<1>(a1, part, buf, bar, t1, wait_ns);
   double rho = t1[0];
   const double n0 = sqrt(rho);
   const double tol = fmax(atol, rtol * n0);
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
         pv[i] = pi;
         ph[i] = dinv[i] * pi;
       }
-      grid_barrier(bar);
+      grid_barrier(bar, wait_ns);
     }
     first = false;
     // v = B phat, alpha = rho / (rhat, v)
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
       a0 = fma(rh[i], y, a0);
     }
     a1[0] = (double)a0;
-    grid_sums<1>(a1, part, buf, bar, t1);
+    grid_sums<1>(a1, part, buf, bar, t1, wait_ns);
     alpha = rho / t1[0];
     if (!isfinite(alpha) || t1[0] == 0.0 || *berr) { done = 2; break; }
     // s = r - alpha v, shat = D^{-1} s, ||s||
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
       a0 = fma(si, si, a0);
     }
     a1[0] = (double)a0;
-    grid_sums<1>(a1, part, buf, bar, t1);
+    grid_sums<1>(a1, part, buf, bar, t1, wait_ns);
     const double ns = sqrt(t1[0]);
     if (!isfinite(ns) || *berr) { done = 2; break; }
     if (ns < tol) {   // converged at s: x += alpha phat
@@ -612,7 +614,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     }
     a2[0] = (double)b0;
     a2[1] = (double)b1;
-    grid_sums<2>(a2, part, buf, bar, t2);
+    grid_sums<2>(a2, part, buf, bar, t2, wait_ns);
     omega = t2[0] / t2[1];
     if (!isfinite(omega) || t2[1] == 0.0 || *berr) { done = 2; break; }
     // r = s - omega t, ||r||, (rhat, r); x += alpha phat + omega shat while the sums
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     a2[1] = (double)b1;
     const unsigned int arrived = grid_sums_begin<2>(a2, part, buf, bar);
     for (int64_t i = i0; i < iend; i += stride) x[i] = x[i] + ta * ph[i] + tom * sh[i];
-    grid_sums_end<2>(part, buf, bar, arrived, t2);
+    grid_sums_end<2>(part, buf, bar, arrived, t2, wait_ns);
     nres = sqrt(t2[0]);
     const double rho_old = rho;
     rho = t2[1];
@@ -669,6 +671,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     sc[S_OMEGA] = omega;
     sc[S_RHO] = rho;
     sc[S_DONE] = *berr ? 2.0 : (double)done;
+    sc[S_BERR] = *berr ? 1.0 : 0.0;
   }
 }
 
@@ -946,6 +949,7 @@ __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restr
 __global__ void k_solver_reset(double* sc, double atol, double rtol, int maxit) {
   if (threadIdx.x == 0) {
     sc[S_DONE] = 0.0;
+    sc[S_BERR] = 0.0;
     sc[S_FIRST] = 1.0;
     sc[S_K_USED] = 0.0;
     sc[S_CYCLE_DONE] = 0.0;
@@ -1053,7 +1057,7 @@ int bicg_fused_launch(afc_problem_s* p, cudaStream_t s, const T* B, const T* din
     cudaEvent_t ev = prof_start(p);
     e = cudaLaunchKernelEx(&cfg, k_bicg_fused<KT, T>, N, p->offs, sc, B, dinv, rhs, xout, x, r, rh, pp, v, sv, t, ph,
                            sh, w.part.p, bar, o->ksp_atol, o->ksp_rtol, o->ksp_maxit,
-                           epi ? *epi : KrylovEpilogue{});
+                           epi ? *epi : KrylovEpilogue{}, (unsigned long long)p->grid_wait_ns);
     prof_stop(p, "k_bicg_fused", ev);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaLaunchKernelEx(k_bicg_fused)");
   });
@@ -1345,6 +1349,13 @@ int krylov_graph(afc_problem_s* p, int system, const afc_opts* o, const double* 
 
 const double* krylov_scalars(afc_problem_s* p) { return p->kw ? p->kw->sc.p : nullptr; }
 int krylov_cycles_slot() { return S_CYCLES; }
+
+int krylov_reset_barrier(afc_problem_s* p) {
+  if (!p->kw || !p->kw->barrier.p) return AFC_OK;
+  AFC_CUDA(cudaMemsetAsync(p->kw->barrier.p, 0, 4 * sizeof(unsigned int), p->stream));
+  AFC_CUDA(cudaStreamSynchronize(p->stream));
+  return AFC_OK;
+}
 const void* krylov_key(afc_problem_s* p) { return p->kw ? (const void*)p->kw->vec.base : nullptr; }
 
 int krylov_solve(afc_problem_s* p, int system, const afc_opts* o, const double* rhs, double* x, int* its,

@@ -28,6 +28,21 @@ std::mutex g_scratch_mutex;
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {};
 
+// Makes the problem's device current for the call and gives the caller's current
+// device back when the call returns.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int device) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != device) err = cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
 int scratch_for(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) {
     set_error("device index out of range for the no-allocation entry point");
@@ -115,12 +130,18 @@ extern "C" int afc_mc_limited_sum_noalloc(afc_problem p, int limiter, const doub
     set_error("limiter must be AFC_LIM_NONE, AFC_LIM_GALERKIN or AFC_LIM_MC");
     return AFC_E_INVALID;
   }
+  if (p->family != AFC_FAMILY_MC && limiter != AFC_LIM_NONE) {
+    // d_ij and the convective entries of the MC family (Remark rem:assembling_mc)
+    set_error("the MC limiter and its Galerkin mode need afc_assemble(..., AFC_FAMILY_MC, ...)");
+    return AFC_E_STATE;
+  }
   if (p->N > kNoAllocMaxNodes) {
     set_error("afc_mc_limited_sum_noalloc accepts at most 262144 nodes (its fixed scratch holds two node vectors); "
               "use afc_mc_limited_sum");
     return AFC_E_INVALID;
   }
-  if (cudaSetDevice(p->device) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  DeviceGuard dg(p->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
   double* scratch = nullptr;
   int st = scratch_for(p->device, &scratch);
   if (st) return st;

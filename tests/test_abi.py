@@ -67,3 +67,34 @@ def test_grid_wait_selftest_rejects_bad_limits_on_host():
         assert afc.afc_selftest_grid_wait(0, bad, C.byref(obs), None) == afc.AFC_E_INVALID
     assert afc.afc_selftest_grid_wait(0, 10.0, None, None) == afc.AFC_E_INVALID
     assert obs.value == -1
+
+
+def test_device_vector_checks_reject_bad_tensors_before_any_call():
+    """afc_mc_limited_sum_noalloc takes raw device pointers, so the binding checks
+    each tensor (CUDA, float64, contiguous, N elements, the problem's device) and
+    raises AFC_E_INVALID before the library could read or write past its end."""
+    torch = pytest.importorskip("torch")
+    from paper_2110_15676_gb300 import afc
+
+    class FakeCuda:   # stands in for a CUDA tensor on this machine without a GPU
+        def __init__(self, n=10, dtype=torch.float64, contiguous=True, index=0):
+            self.is_cuda, self.dtype, self._c, self._n = True, dtype, contiguous, n
+            self.device = type("dev", (), {"index": index})()
+
+        def data_ptr(self):
+            return 0
+
+        def is_contiguous(self):
+            return self._c
+
+        def numel(self):
+            return self._n
+
+    afc.check_device_vector(FakeCuda(), 10, 0, "u", "t")     # accepted
+    cases = [(torch.zeros(10, dtype=torch.float64), "CUDA"), (FakeCuda(dtype=torch.float32), "dtype"),
+             (FakeCuda(contiguous=False), "contiguous"), (FakeCuda(n=9), "elements"),
+             (FakeCuda(index=1), "cuda:1"), (np.zeros(10), "tensor")]
+    for t, why in cases:
+        with pytest.raises(afc.AfcError) as e:
+            afc.check_device_vector(t, 10, 0, "u", "afc_mc_limited_sum_noalloc")
+        assert e.value.status == afc.AFC_E_INVALID and why in str(e.value)

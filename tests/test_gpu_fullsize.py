@@ -8,6 +8,9 @@
   (the limiter of row i reaches three element layers), plus the limiter-level bound
   dt F*_i / m_i in [Q_i^-, Q_i^+] and conservation at full size, and one complete CN
   step whose returned residual meets the stopping rule.
+* The benchmarked Q1 65^3 CN step itself (CFL 1, six fixed-point corrections with
+  tight inner solves) through afc_step against the oracle's step, the whole field at
+  the 1e-10 relative bound per step.
 Inputs are seeded fields from the workload generators; nothing the oracle sees comes
 from the GPU."""
 import math
@@ -82,9 +85,20 @@ def test_mc_sweep_full_size_p1_129(afc):
         assert abs(F[i] - Fo[loc]) <= 1e-13 * scale, i
         assert out["umax"][i] == fl["u"][prob.MC[loc].indices].max()
         assert out["umin"][i] == fl["u"][prob.MC[loc].indices].min()
-    # the sweep the bench times runs on the same problem
+    # the sweep the bench times, on the same problem: its residual f + F* - AA u at the
+    # sampled rows against the oracle's (Sec. 4), 0 on Dirichlet rows
     P.set_solution(u)
     P.mc_residual_sweep(afc.AFC_LIM_MC)
+    res = P.get_residual()
+    assert (res[wl.dir_mask.astype(bool)] == 0).all()
+    rscale = np.abs(res).max()
+    assert rscale > 0
+    for i in _samples(np.random.default_rng(130), wl, 24):
+        prob, gid, loc, fl = _sub_problem(wl, "mc", i, 3, {"u": u})
+        rstar, _ = O.mc_limited_fluxes(prob, fl["u"])
+        Fo = O.limited_sum(prob, np.ones_like(rstar), rstar)
+        ro = prob.f[loc] + Fo[loc] - (prob.AA @ fl["u"])[loc]
+        assert abs(res[i] - ro) <= 1e-13 * rscale, i
 
 
 def test_cn_limiter_and_step_full_size_q1_65(afc):
@@ -124,10 +138,35 @@ def test_cn_limiter_and_step_full_size_q1_65(afc):
         Fo = O.limited_sum(prob, alpha, r)
         assert abs(F[i] - Fo[loc]) <= 1e-13 * scale, i
         assert abs(ut[i] - ut_l[loc]) <= 1e-15 * max(1.0, abs(ut_l[loc]))
-    # one complete step of the benchmark workload
+    # one complete step of the benchmark workload, run to its stopping rule
     dt_cfl = P.cfl_timestep(1.0)
     P.set_solution(wl.u0)
     st = P.step(afc.default_opts(scheme=afc.AFC_CN_NONLINEAR, dt=dt_cfl, fp_tol=1e-10, ksp_atol=1e-12))
     assert st["status"] == afc.AFC_OK
     assert st["res_final"] < math.sqrt(P.N) * 1e-10
     assert st["outer_its"] >= 2 and st["inner_its"] >= st["outer_its"]
+
+
+def test_cn_step_full_size_q1_65_matches_oracle(afc):
+    """The step bench.py times (nonlinear Zal+CN, Q1 65^3, CFL 1, prelimiting, FP64),
+    at a fixed count of six fixed-point corrections and inner BiCGStab to 1e-14, so that
+    neither side's stopping test decides the iterate: every node against the oracle's
+    cn_step with the same settings, relative max-norm 1e-10."""
+    wl = W.rotating_transient("q1", 65)
+    mesh = O.structured_mesh(wl.elem, wl.n)
+    o = O.assemble(mesh, wl.eps, wl.b, wl.c, wl.f, wl.dir_mask.astype(bool), wl.u_dir)
+    dt = O.cfl_timestep(o, 1.0)
+    u_ref, sto = O.cn_step(o, wl.u0, dt, fixed_iterations=6, ksp_atol=1e-14)
+    P = afc.Problem.structured(wl.elem, wl.n)
+    P.set_coefficients(wl.eps, wl.b, wl.c, wl.f)
+    P.set_dirichlet(wl.dir_mask, wl.u_dir)
+    P.assemble(afc.AFC_FAMILY_FCT, afc.AFC_FP64)
+    assert abs(P.cfl_timestep(1.0) - dt) <= 1e-14 * dt
+    for graph in (1, 0):
+        P.set_solution(wl.u0)
+        st = P.step(afc.default_opts(scheme=afc.AFC_CN_NONLINEAR, dt=dt, fp_fixed_its=6, ksp_atol=1e-14,
+                                     graph=graph))
+        assert st["outer_its"] == 6 == sto["outer_its"]
+        u = P.get_solution()
+        err = np.abs(u - u_ref).max() / np.abs(u_ref).max()
+        assert err <= 1e-10, (graph, err)

@@ -57,6 +57,24 @@ def test_noalloc_matches_allocating_entry_point_twice(cuda, elem, n):
         assert np.abs(out.cpu().numpy() - ref).max() <= PASS_TOL * max(np.abs(ref).max(), 1e-300)
 
 
+def test_noalloc_needs_the_mc_family(cuda):
+    torch, afc = cuda
+    wl = W.stationary_inflow("p1", 9)
+    P = afc.Problem.structured(wl.elem, wl.n)
+    P.set_coefficients(wl.eps, wl.b, wl.c, wl.f)
+    P.set_dirichlet(wl.dir_mask, wl.u_dir)
+    P.assemble(afc.AFC_FAMILY_FCT, afc.AFC_FP64)
+    u = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+    out = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+    for lim in (afc.AFC_LIM_MC, afc.AFC_LIM_GALERKIN):
+        with pytest.raises(afc.AfcError) as e:
+            P.mc_limited_sum_noalloc(u, out, lim)
+        assert e.value.status == afc.AFC_E_STATE
+    P.mc_limited_sum_noalloc(u, out, afc.AFC_LIM_NONE)   # alpha = 0 needs no MC data
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(cuda):
     torch, afc = cuda
     P = _mc_problem(afc, "p1", 65)              # 274,625 nodes > 262,144
