@@ -385,11 +385,17 @@ def batched(afc, W, torch, stream, steps=50, count=256, seed=4, shape=None, solo
             "batched_fp64_bitwise_equal_to_one_at_a_time": same}
 
 
-def serving(afc, W, rates=(20.0, 100.0, 500.0), count=48, seed=5, stat_maxit=50):
+def serving(afc, W, rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), count=48, seed=5, stat_maxit=1000,
+            serial_rates=(10.0, 500.0)):
     """Poisson streams of stationary and transient CDR requests (P1 or Q1, nodes per
     side uniform in [17, 97], eps log-uniform [1e-8, 1e-4], c uniform [0, 1]):
     the batched server with mixed precision against the serial server with FP64
-    (one request at a time), latency p50 / p99 and solves/s per arrival rate."""
+    (one request at a time), latency p50 / p99 and solves/s per arrival rate.  Only
+    converged results count: a stationary request that ends AFC_NOT_CONVERGED (the
+    fixed point did not reach its tolerance within stat_maxit iterations) is
+    reported as not converged and left out of solves/s and the latencies.  The
+    serial arm runs at `serial_rates` only: one request at a time, it is saturated
+    at every rate of the sweep."""
     mix = W.serving_mix(np.random.default_rng(seed), count)
 
     def opts(kind, prec):
@@ -414,7 +420,9 @@ def serving(afc, W, rates=(20.0, 100.0, 500.0), count=48, seed=5, stat_maxit=50)
         arr = np.cumsum(np.random.default_rng(int(seed * 1000 + rate)).exponential(1.0 / rate, size=count))
         row = {"rate_per_s": rate}
         for name, (mode, rq) in arms.items():
-            with afc.Server(mode=mode, stationary_workers=4, max_chunk=10) as srv:
+            if name == "serial_fp64" and rate not in serial_rates:
+                continue
+            with afc.Server(mode=mode, stationary_workers=8, max_chunk=10, builders=4) as srv:
                 t0 = time.perf_counter()
                 ids = []
                 for t_arr, r in zip(arr, rq):
@@ -422,14 +430,17 @@ def serving(afc, W, rates=(20.0, 100.0, 500.0), count=48, seed=5, stat_maxit=50)
                     if dt > 0:
                         time.sleep(dt)
                     ids.append(srv.submit(r))
-                lat, done, first, states, failed = [], [], None, [], []
+                lat, done, first, conv, failed, fp_its = [], [], None, [], [], []
                 for q, rid in enumerate(ids):
                     res, u = srv.wait(rid, timeout=-1.0, want_u=(rate == rates[-1]))
-                    states.append(res["state"])
-                    if res["state"] != afc.AFC_REQ_DONE:
+                    ok = res["state"] == afc.AFC_REQ_DONE and res["status"] == afc.AFC_OK
+                    conv.append(ok)
+                    if not ok:
                         kind, wl = mix[q]
                         failed.append({"request": q, "kind": kind, "name": wl.name, "state": res["state"],
                                        "status": res["status"], "message": res["message"]})
+                    if mix[q][0] == "stationary":
+                        fp_its.append(res["stats"]["outer_its"])
                     lat.append(res["t_done"] - res["t_submit"])
                     done.append(res["t_done"])
                     first = res["t_submit"] if first is None else min(first, res["t_submit"])
@@ -438,25 +449,68 @@ def serving(afc, W, rates=(20.0, 100.0, 500.0), count=48, seed=5, stat_maxit=50)
                     srv.release(rid)
                 info = srv.info()
             lat = np.asarray(lat) * 1e3
+            conv = np.asarray(conv)
             span = max(done) - first
-            row[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                         "solves_per_s": count / span, "makespan_s": span,
-                         "done": int(sum(s == afc.AFC_REQ_DONE for s in states)),
-                         "max_batch": info["max_batch"], "chunks": info["chunks"], "not_done": failed,
-                         "p50_ms_by_kind": {k: float(np.percentile([l for l, (kk, _) in zip(lat, mix) if kk == k], 50))
+            lc = lat[conv] if conv.any() else np.asarray([np.nan])
+            row[name] = {"p50_ms": float(np.percentile(lc, 50)), "p99_ms": float(np.percentile(lc, 99)),
+                         "solves_per_s": int(conv.sum()) / span, "makespan_s": span,
+                         "converged": int(conv.sum()), "not_converged": failed,
+                         "stationary_fp_its_mean": float(np.mean(fp_its)) if fp_its else None,
+                         "max_batch": info["max_batch"], "chunks": info["chunks"],
+                         "mean_batch": info["instance_steps"] / info["batched_steps"] if info["batched_steps"] else None,
+                         "p50_ms_by_kind": {k: float(np.percentile([l for l, c, (kk, _) in zip(lat, conv, mix)
+                                                                    if kk == k and c] or [np.nan], 50))
                                             for k in ("stationary", "transient")}}
-        row["speedup_solves_per_s"] = row["batched_mixed"]["solves_per_s"] / row["serial_fp64"]["solves_per_s"]
+        if "serial_fp64" in row:
+            row["speedup_solves_per_s"] = row["batched_mixed"]["solves_per_s"] / row["serial_fp64"]["solves_per_s"]
         rows.append(row)
     diff = max((float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
-                for a, b in zip(sols["batched_mixed"], sols["serial_fp64"]) if np.abs(a).max() > 0), default=None)
+                for a, b in zip(sols.get("batched_mixed", []), sols.get("serial_fp64", [])) if np.abs(a).max() > 0),
+               default=None)
     n_st = sum(k == "stationary" for k, _ in mix)
-    return {"workload": f"{count} requests (numpy default_rng({seed})): {n_st} stationary MC (inflow problem, omega 0.5, "
-                        f"tol 1e-8, at most {stat_maxit} fixed-point iterations, Jacobi-GMRES(20) rtol 1e-6), "
-                        f"{count - n_st} transient SSP3 Zalesak (50 steps, CFL 0.5); P1/Q1, n in [17, 97], eps "
-                        f"log-uniform [1e-8, 1e-4], c in [0, 1]; Poisson arrivals",
+    return {"workload": f"{count} requests per rate (numpy default_rng({seed})): {n_st} stationary MC (inflow problem, "
+                        f"omega 0.5, tol 1e-8, at most {stat_maxit} fixed-point iterations, Jacobi-GMRES(20) rtol "
+                        f"1e-6), {count - n_st} transient SSP3 Zalesak (50 steps, CFL 0.5); P1/Q1, n in [17, 97], "
+                        f"eps log-uniform [1e-8, 1e-4], c in [0, 1]; Poisson arrivals",
             "rates": rows, "mixed_max_rel_diff_vs_fp64": diff,
-            "arms": "batched_mixed: continuous batching of transient requests, 4 concurrent stationary solves, "
-                    "FP32 inner solves / fluxes; serial_fp64: one request at a time, FP64"}
+            "arms": "batched_mixed: 4 builders, continuous batching of transient requests, 8 concurrent stationary "
+                    "solves, FP32 inner solves / fluxes, float-pair MC residual; serial_fp64: one request at a time, "
+                    f"FP64, at rates {list(serial_rates)}"}
+
+
+def _summary(value, e2e, roof, mixed, sweep, bat, srv, cpu):
+    """The headline numbers of every leg in a few hundred bytes (the full records follow)."""
+    r3 = lambda x: None if x is None else float(f"{x:.4g}")   # noqa: E731
+    out = {"cn_q1_65": {"dof_iters_per_s": r3(value), "e2e": r3(e2e["value"]),
+                        "mixed": r3(mixed["value"]) if mixed else None,
+                        "top_kernel": roof["kernel"] if roof else None, "top_frac_fp64": r3(roof["frac"]) if roof else None}}
+    if sweep:
+        out["mc_sweep_p1_129"] = {"ms": r3(sweep["ms_per_sweep"]), "hbm_frac": r3(sweep["hbm"]["frac"]),
+                                  "hbm_gbs": r3(sweep["hbm"]["achieved"])}
+        if sweep.get("solve"):
+            sv = sweep["solve"]
+            out["mc_solve_p1_129"] = {"s": r3(sv["ms"] / 1e3), "fp_its": sv["fixed_point_its"],
+                                      "gmres_its": sv["gmres_its"], "umin": r3(sv["umin"])}
+    if bat:
+        out["batched_256"] = {"mixed_solves_per_s": r3(bat["batched_mixed"]["solves_per_s"]),
+                              "fp64_solves_per_s": r3(bat["batched_fp64"]["solves_per_s"]),
+                              "one_at_a_time_fp64_solves_per_s": r3((bat["one_at_a_time_fp64"] or {}).get("solves_per_s")),
+                              "speedup": r3(bat["speedup_mixed_vs_one_at_a_time_fp64"]),
+                              "mixed_rel_diff": r3(bat["mixed_rel_diff_vs_fp64"])}
+    if srv:
+        out["serving"] = [{"rate": r["rate_per_s"],
+                           "batched": [r3(r["batched_mixed"]["solves_per_s"]), r3(r["batched_mixed"]["p50_ms"]),
+                                       r3(r["batched_mixed"]["p99_ms"]), r["batched_mixed"]["max_batch"],
+                                       r3(r["batched_mixed"]["mean_batch"]), r["batched_mixed"]["converged"]],
+                           "serial": [r3(r["serial_fp64"]["solves_per_s"]), r3(r["serial_fp64"]["p50_ms"]),
+                                      r3(r["serial_fp64"]["p99_ms"]), r["serial_fp64"]["converged"]]
+                           if "serial_fp64" in r else None} for r in srv["rates"]]
+        out["serving_fields"] = ("batched: solves/s, p50 ms, p99 ms, max batch, mean batch, converged; "
+                                 "serial: solves/s, p50 ms, p99 ms, converged")
+    if cpu:
+        out["cpu"] = {"dof_iters_per_s": r3(cpu["value"]), "cores": cpu["cores"],
+                      "single_thread": r3(cpu["single_thread"]["value"])}
+    return out
 
 
 def run_ours(args, ws, rank, local):
@@ -576,7 +630,7 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_sample_its)
+        cpu = cpu_baseline(args.cpu_rounds)
 
     # every profiled kernel with its algorithmic FP64 work: achieved rate and fraction of the pipe
     kernel_table = {}
@@ -589,6 +643,7 @@ def run_ours(args, ws, rank, local):
         kernel_table[k] = row
 
     if rank == 0:
+        summary = _summary(value, e2e, roof, mixed, sweep, bat, srv, cpu)
         line = {
             "metric": METRIC, "value": value, "unit": "dof-iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1), "higher_is_better": True,
@@ -596,11 +651,13 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD, "dofs": N, "nnz": nnz, "edges": E, "dt": dt,
                        "fixed_point_its": its_total, "krylov_its": inner_total,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
+            "summary": summary,
             "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
             "kernels": kernel_table,
             "kernel_times": "second pass of the same steps, launches issued one by one with per-launch CUDA "
                             "events (the timed pass runs each step as one CUDA graph)",
             "mixed": mixed, "mc_sweep": sweep, "batched": bat, "serving": srv, "cpu_baseline": cpu,
+            "summary_again": summary,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -617,42 +674,115 @@ def _oracle_problem():
     return O, o, wl, dt
 
 
-def cpu_baseline(sample_its: int) -> dict:
-    """The CPU oracle, as it stands, on a bounded sample of the same workload: the
-    first `sample_its` fixed-point corrections of one CN step (single thread)."""
-    O, o, wl, dt = _oracle_problem()
+# The CPU unit of work, the same for the CPU baseline and the reference arm: one call of
+# the oracle's CN step from u0 with a single fixed-point correction (its predictor, its
+# system matrix, one limiter pass, one BiCGStab solve to atol 1e-12, the update).
+_ORACLE = {}
+
+
+def _oracle_worker_init():
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    _ORACLE["p"] = _oracle_problem()
+
+
+def _oracle_unit(_=None):
+    O, o, wl, dt = _ORACLE["p"]
     t0 = time.perf_counter()
-    _, st = O.cn_step(o, wl.u0, dt, tol=FP_TOL, ksp_atol=KSP_ATOL, fixed_iterations=sample_its)
-    sec = time.perf_counter() - t0
-    N = o.mesh.n_nodes
-    return {"value": N * st["outer_its"] / sec, "unit": "dof-iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{st['outer_its']} fixed-point corrections of one CN step on the same 65^3 Q1 problem "
-                      f"({sec:.1f} s)"}
+    _, st = O.cn_step(o, wl.u0, dt, tol=FP_TOL, ksp_atol=KSP_ATOL, fixed_iterations=1)
+    return st["outer_its"], time.perf_counter() - t0
+
+
+def _host_cores():
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return n, model
+
+
+class OraclePool:
+    """The oracle on every host core: one spawned process per core (spawn, so that no
+    child inherits a CUDA context), each with the problem assembled once and one BLAS
+    thread; a round runs one unit per core and is timed on the parent's clock."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init)
+        self.pool.map(_oracle_unit, range(procs))     # warm-up round (and assembly)
+
+    def round(self):
+        t0 = time.perf_counter()
+        its = sum(i for i, _ in self.pool.map(_oracle_unit, range(self.procs)))
+        return its, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(rounds: int) -> dict:
+    """The CPU oracle, as it stands, on a bounded sample of the same workload: the
+    unit above (one CN step with one fixed-point correction), one thread, and all host
+    cores (one process per core) for `rounds` rounds."""
+    _oracle_worker_init()
+    N = _ORACLE["p"][1].mesh.n_nodes
+    _oracle_unit()
+    its1, sec1 = 0, 0.0
+    for _ in range(rounds):
+        i, t = _oracle_unit()
+        its1 += i
+        sec1 += t
+    cores, model = _host_cores()
+    pool = OraclePool(cores)
+    itsc, secc = 0, 0.0
+    for _ in range(rounds):
+        i, t = pool.round()
+        itsc += i
+        secc += t
+    pool.close()
+    unit = "one oracle CN step (Q1 65^3) with one fixed-point correction"
+    return {"value": N * itsc / secc, "unit": "dof-iters/s", "cores": cores, "kind": "oracle", "cpu": model,
+            "sample": f"{rounds} rounds of {cores} concurrent units ({unit}), one per core ({secc:.1f} s)",
+            "single_thread": {"value": N * its1 / sec1, "cores": 1,
+                              "sample": f"{rounds} units ({unit}) on one thread ({sec1:.1f} s)"}}
 
 
 def run_reference(args, ws, rank):
-    """Reference arm: the CPU oracle timed on the same workload; each step is a
-    bounded sample (one fixed-point correction of a CN step)."""
+    """Reference arm: the CPU oracle timed on the same workload and unit as the CPU
+    baseline; each step is one round of one unit per host core."""
     if rank != 0:
         return
+    cores, model = _host_cores()
+    pool = OraclePool(cores)
     O, o, wl, dt = _oracle_problem()
     N = o.mesh.n_nodes
-    u = wl.u0.copy()
     for _ in range(args.warmup):
-        O.cn_step(o, u, dt, tol=FP_TOL, ksp_atol=KSP_ATOL, fixed_iterations=1)
-    t0 = time.perf_counter()
-    its = 0
+        pool.round()
+    its, sec = 0, 0.0
     for _ in range(args.steps):
-        _, st = O.cn_step(o, u, dt, tol=FP_TOL, ksp_atol=KSP_ATOL, fixed_iterations=1)
-        its += st["outer_its"]
-    sec = time.perf_counter() - t0
+        i, t = pool.round()
+        its += i
+        sec += t
+    pool.close()
     value = N * its / sec
+    sample = (f"per step one round of {cores} concurrent units (one oracle CN step with one fixed-point "
+              f"correction each), one per host core")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "dof-iters/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dofs": N, "sample": "one fixed-point correction of a CN step per step"},
-            "cpu_baseline": {"value": value, "unit": "dof-iters/s", "cores": 1, "kind": "oracle",
-                             "sample": "one fixed-point correction of a CN step per step"},
+            "config": {"workload": WORKLOAD, "dofs": N, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "dof-iters/s", "cores": cores, "kind": "oracle", "cpu": model,
+                             "sample": sample},
             "e2e": {"value": value, "unit": "dof-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -677,7 +807,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--only-serving", action="store_true", help="time only the request-server streams")
     ap.add_argument("--serving-count", type=int, default=48)
-    ap.add_argument("--cpu-sample-its", type=int, default=6)
+    ap.add_argument("--cpu-rounds", type=int, default=2, help="timed rounds of the CPU baseline")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

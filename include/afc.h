@@ -99,7 +99,9 @@ typedef struct {
   int32_t gmres_restart;  /* GMRES(m) restart length, 1..32                               */
   int32_t precision;      /* afc_precision: AFC_MIXED runs the inner solve (CN, stationary)*/
                           /* or the raw fluxes r_ij (SSP) in FP32; limiter sums, alpha    */
-                          /* and the lumped-mass update stay FP64                         */
+                          /* and the lumped-mass update stay FP64; the stationary MC      */
+                          /* residual and clip run in float pairs (see                    */
+                          /* afc_mc_residual_sweep)                                       */
   int32_t prelimit;       /* CN: apply Eq. prelimiting (L = 2)                            */
   int32_t graph;          /* 1: run the whole step / solve as one CUDA graph with the     */
                           /* loop control on the device (default); 0: host-driven loop    */
@@ -113,6 +115,14 @@ typedef struct {
   double res0;            /* first nonlinear residual norm                                */
   double res_final;       /* last nonlinear residual norm                                 */
   double umin, umax;      /* extremes of the returned solution                            */
+  double dmp_violation;   /* max(0, lo - umin, umax - hi): how far the returned solution  */
+                          /* lies outside [lo, hi], the range of the call's input state   */
+                          /* and of the Dirichlet values.  The discrete maximum principle */
+                          /* of the limited schemes (Sec. 2.1.3, Eq. MClimiter) keeps it  */
+                          /* at rounding level for f = 0, c = 0 (the stationary solve: at */
+                          /* the level of its tolerance); a source can raise u above hi   */
+  double t_ms;            /* host wall time of the call (per-kernel device times: see     */
+                          /* afc_profile)                                                 */
 } afc_stats;
 
 /* ---- lifetime -------------------------------------------------------------- */
@@ -237,7 +247,11 @@ int afc_mc_limited_sum_noalloc(afc_problem p, int limiter, const double* u, doub
 /* One limiter + residual sweep of the stationary problem on the stored solution:
  * bounds (Eq. u_max_min), limited fluxes (Eq. MClimiter, or alpha = 1 / 0 per
  * `limiter`) and res = f + F*(u) - AA u into internal buffers.  Only enqueued on
- * the problem's stream (no synchronisation, no host copy): for timing the sweep. */
+ * the problem's stream (no synchronisation, no host copy): for timing the sweep.
+ * On a mixed-precision assembly the MC and Galerkin sweeps run as the stationary
+ * solve with AFC_MIXED runs them: in float-pair arithmetic on the FP32 pipe (values
+ * carried as two floats, 48 significand bits), which agrees with the FP64 sweep to
+ * ~1e-14 of the magnitudes summed.  Values must stay below 2^127 in magnitude. */
 int afc_mc_residual_sweep(afc_problem p, int limiter);
 
 /* Copy out (host array of N) the nonlinear residual res = f + F*(u) - AA u of the
@@ -318,9 +332,10 @@ int afc_batch_info(afc_batch b, int64_t* total_nodes, int64_t* launches);
  * A server solves requests (a transient SSP run or a stationary solve of one CDR
  * problem on a box grid) submitted from any thread, with the problems' data
  * resident on the device while they run:
- *  - AFC_SERVE_BATCHED: an admission thread admits requests in arrival order
+ *  - AFC_SERVE_BATCHED: admission threads admit requests in arrival order
  *    while their estimated device memory fits the budget and the slot count
- *    allows, and builds their problems; all admitted transient requests advance
+ *    allows, and build their problems, `builders` at once; all admitted transient
+ *    requests advance
  *    together in batched SSP steps (afc_batch_step), in chunks of at most
  *    max_chunk steps, and requests admitted meanwhile join at the next chunk;
  *    stationary requests run concurrently, each on its own stream, on
@@ -361,7 +376,8 @@ typedef struct {
 typedef struct {
   int32_t state;          /* afc_request_state                                             */
   int32_t status;         /* afc_status of the solve                                       */
-  afc_stats stats;        /* transient: stages, umin, umax; stationary: as afc_solve_stationary */
+  afc_stats stats;        /* transient: stages, umin, umax, the largest dmp_violation of its    */
+                          /* steps; stationary: as afc_solve_stationary                    */
   int64_t n_nodes;
   double t_submit, t_admit, t_done;   /* seconds on the server's clock                     */
   char message[160];      /* FAILED: the library's error detail                            */
@@ -373,6 +389,8 @@ typedef struct {
   int64_t hbm_budget;         /* device bytes admitted requests may hold (estimated)       */
   int32_t stationary_workers; /* concurrent stationary solves (1..64)                      */
   int32_t max_chunk;          /* transient steps per batched call                          */
+  int32_t builders;           /* AFC_SERVE_BATCHED: requests whose problems are built at   */
+                              /* once (1..64; admission stays in arrival order)            */
 } afc_serve_config;
 
 typedef struct {
@@ -380,6 +398,8 @@ typedef struct {
   int64_t chunks;             /* batched calls issued                                      */
   int64_t batched_steps;      /* steps advanced by those calls                             */
   int64_t max_batch;          /* most transient requests in one batch                      */
+  int64_t instance_steps;     /* steps times instances of those calls: instance_steps /    */
+                              /* batched_steps is the mean batch size over steps           */
   double clock;               /* seconds since the server started                          */
 } afc_serve_info;
 

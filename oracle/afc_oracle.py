@@ -825,3 +825,74 @@ def p1_error_norms(mesh: Mesh, uh, exact, nq: int = 4, chunk: int = 20000):
         e1 += float((d * W[None]).sum(axis=1) @ six_vol)
         e2 += float((d * d * W[None]).sum(axis=1) @ six_vol)
     return e1, math.sqrt(e2)
+
+
+# --------------------------------------------------------------------------
+# L2 error of a Q1 solution on a uniform grid of the unit cube against an
+# indicator function (the error the rotating-shapes example reports)
+# --------------------------------------------------------------------------
+def q1_mass_form(n: int, u):
+    """u^T M u for the consistent Q1 mass matrix of the uniform grid of the unit cube
+    with n nodes per side: M is the tensor product of the 1D P1 mass matrices
+    (h / 6) [2 1; 1 2] per interval, so the form is three 1D products."""
+    h = 1.0 / (n - 1)
+    U = np.asarray(u, dtype=np.float64).reshape(n, n, n)   # (z, y, x), x fastest
+
+    def m1(V, axis):
+        V = np.moveaxis(V, axis, 0)
+        W = 4.0 * V
+        W[0] -= 2.0 * V[0]
+        W[-1] -= 2.0 * V[-1]
+        W[1:] += V[:-1]
+        W[:-1] += V[1:]
+        return np.moveaxis(W * (h / 6.0), 0, axis)
+
+    return float((U * m1(m1(m1(U, 0), 1), 2)).sum())
+
+
+def q1_indicator_integrals(n: int, u, chi, box, m: int = 4, slab: int = 4):
+    """(int u_h chi, int chi^2) over the cells of the uniform Q1 grid in the index box
+    `box` = ((x0, x1), (y0, y1), (z0, z1)) of cell indices (outside it chi must
+    vanish), u_h the trilinear interpolant of the nodal values u, by the tensor Gauss
+    rule with m points per direction in every cell."""
+    h = 1.0 / (n - 1)
+    g, w = np.polynomial.legendre.leggauss(m)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    Wq = (w[:, None, None] * w[None, :, None] * w[None, None, :]).ravel() * h ** 3
+    ref = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)          # (Q, 3)
+    # trilinear basis at the points, local vertex k = dx + 2 dy + 4 dz
+    phi = np.stack([(ref[:, 0] if dx else 1 - ref[:, 0]) * (ref[:, 1] if dy else 1 - ref[:, 1]) *
+                    (ref[:, 2] if dz else 1 - ref[:, 2])
+                    for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)], axis=1)   # (Q, 8)
+    U = np.asarray(u, dtype=np.float64).reshape(n, n, n)
+    (x0, x1), (y0, y1), (z0, z1) = box
+    cx = np.arange(x0, x1)
+    cy = np.arange(y0, y1)
+    s_uc = 0.0
+    s_c = 0.0
+    for za in range(z0, z1, slab):
+        cz = np.arange(za, min(za + slab, z1))
+        CZ, CY, CX = np.meshgrid(cz, cy, cx, indexing="ij")
+        CZ, CY, CX = CZ.ravel(), CY.ravel(), CX.ravel()
+        px = (CX[:, None] + ref[None, :, 0]) * h
+        py = (CY[:, None] + ref[None, :, 1]) * h
+        pz = (CZ[:, None] + ref[None, :, 2]) * h
+        C = chi(px, py, pz)                                           # (cells, Q)
+        if not C.any():
+            continue
+        s_c += float((C * C * Wq[None]).sum())
+        corner = np.stack([U[CZ + dz, CY + dy, CX + dx] for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)],
+                          axis=1)                                     # (cells, 8)
+        uq = corner @ phi.T                                           # (cells, Q)
+        s_uc += float((uq * C * Wq[None]).sum())
+    return s_uc, s_c
+
+
+def q1_l2_error_indicator(n: int, u, chi, box, m: int = 4):
+    """||u_h - chi||_{L2} = sqrt(u^T M u - 2 int u_h chi + int chi^2): the first term
+    exact, the other two by the Gauss rule of q1_indicator_integrals (for an
+    indicator chi^2 = chi)."""
+    uc, c = q1_indicator_integrals(n, u, chi, box, m)
+    return math.sqrt(max(q1_mass_form(n, u) - 2.0 * uc + c, 0.0))

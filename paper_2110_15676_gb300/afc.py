@@ -55,7 +55,8 @@ class afc_opts(C.Structure):
 
 class afc_stats(C.Structure):
     _fields_ = [("outer_its", C.c_int32), ("inner_its", C.c_int32), ("stages", C.c_int32), ("status", C.c_int32),
-                ("res0", C.c_double), ("res_final", C.c_double), ("umin", C.c_double), ("umax", C.c_double)]
+                ("res0", C.c_double), ("res_final", C.c_double), ("umin", C.c_double), ("umax", C.c_double),
+                ("dmp_violation", C.c_double), ("t_ms", C.c_double)]
 
 
 class afc_batch_tuning(C.Structure):
@@ -79,13 +80,14 @@ class afc_result(C.Structure):
 
 class afc_serve_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("max_active", C.c_int32), ("hbm_budget", C.c_int64),
-                ("stationary_workers", C.c_int32), ("max_chunk", C.c_int32)]
+                ("stationary_workers", C.c_int32), ("max_chunk", C.c_int32), ("builders", C.c_int32)]
 
 
 class afc_serve_info(C.Structure):
     _fields_ = [("pending", C.c_int64), ("active", C.c_int64), ("bytes_in_use", C.c_int64),
                 ("completed", C.c_int64), ("failed", C.c_int64), ("chunks", C.c_int64),
-                ("batched_steps", C.c_int64), ("max_batch", C.c_int64), ("clock", C.c_double)]
+                ("batched_steps", C.c_int64), ("max_batch", C.c_int64), ("instance_steps", C.c_int64),
+                ("clock", C.c_double)]
 
 
 _P = C.c_void_p

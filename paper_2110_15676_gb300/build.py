@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libafc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mesh.cpp", "prof.cpp", "assemble.cu", "fct.cu", "mc.cu", "krylov.cu", "api.cu", "noalloc.cu", "graph.cu", "batch.cu", "serve.cpp", "selftest.cu"]
+SOURCES = ["mesh.cpp", "prof.cpp", "assemble.cu", "fct.cu", "mc.cu", "mc_pair.cu", "krylov.cu", "api.cu", "noalloc.cu", "graph.cu", "batch.cu", "serve.cpp", "selftest.cu"]
 
 
 def nvcc() -> str:

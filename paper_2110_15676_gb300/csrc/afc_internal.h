@@ -150,6 +150,12 @@ struct afc_problem_s {
   afc::DBuf<double> Fold;           // CN with the MC limiter: F*(u^{n-1})
   afc::DBuf<unsigned int> clip;     // MC: per row, bit ku set if the pair (i, i + o) was clipped
   afc::DBuf<float4> nodef;          // MC: (u, u_max - u, u - u_min) rounded to single
+  // MC, mixed precision: the sweep in float pairs (mc_pair.cu)
+  afc::DBuf<float2> AGp, fp2;       // K * N and N: AG and f as pairs
+  afc::DBuf<float> pairf_lo;        // 3 * Kup * N: low parts of 2|d_ij|, k_ij, k_ji
+  afc::DBuf<float2> up2, yp2;       // node vectors: u and y = f - AG u as pairs
+  afc::DBuf<float2> abh2, abl2;     // node vectors: high and low parts of (A, B) = (u_max - u, u - u_min)
+  afc::DBuf<float2> cp_up;          // Kup * N: clipped amount of each pair, at its lower row
   afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
   // mixed-precision explicit stage: m_ij, d_ij, r_ij (Kup * N) and u, udot^L (node vectors) in single
   afc::DBuf<float> m32_up, d32_up, r32, uf, udf;
@@ -164,6 +170,11 @@ struct afc_problem_s {
   afc::StepGraph* g_stat = nullptr;   // cached graph of afc_solve_stationary
   cudaStream_t cap_stream = nullptr;  // private stream used to capture graphs
   int64_t launches = 0;             // kernel launches issued on this problem
+  // range of the stored solution (known after afc_set_solution, a step or a solve)
+  // and of the Dirichlet values: the reference of afc_stats.dmp_violation
+  bool u_range_valid = false;
+  double u_lo = 0.0, u_hi = 0.0;
+  double dir_lo = 1e308, dir_hi = -1e308;
   // bounded-wait limit of the grid barriers in this problem's persistent launches
   unsigned long long grid_wait_ns = 4000000000ull;
   int64_t device_bytes = 0;
@@ -197,8 +208,14 @@ int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int li
 // MC
 // transient MC stage: bounds of u and the clipped SSP fluxes r*_ij into r_up (after the rate pass)
 int mc_ssp_fluxes(afc_problem_s* p, const double* u);
+// pair = true: the MC and Galerkin modes of a mixed-precision assembly evaluate the
+// residual in float pairs (mc_pair.cu); F* for inspection and the other modes stay FP64
 int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot,
-                        bool want_F = false);
+                        bool want_F = false, bool pair = false);
+// the same residual (MC or Galerkin) in float-pair arithmetic, for mixed-precision MC
+// problems (mc_pair.cu); mc_pair_setup builds its pair copies at assembly
+int mc_pair_setup(afc_problem_s* p);
+int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot);
 
 // ---- reductions and BLAS-1 (krylov.cu) ----
 int dot_device(afc_problem_s* p, const double* x, const double* y, double* out_slot);

@@ -2,6 +2,7 @@
 // and the drivers of the hot path (explicit SSP stages, the Crank-Nicolson and
 // stationary fixed-point loops of Sec. 4).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -115,6 +116,8 @@ void destroy_all(afc_problem_s* p) {
   p->Bst32.free_(); p->dinv_st32.free_(); p->Bcn32.free_(); p->dinv_cn32.free_();
   p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_(); p->clip.free_();
   p->pairf.free_(); p->nodef.free_();
+  p->AGp.free_(); p->fp2.free_(); p->pairf_lo.free_(); p->up2.free_(); p->yp2.free_(); p->abh2.free_(); p->abl2.free_();
+  p->cp_up.free_();
   p->m32_up.free_(); p->d32_up.free_(); p->r32.free_(); p->uf.free_(); p->udf.free_();
   if (p->host_scal) cudaFreeHost(p->host_scal);
   delete p;
@@ -288,6 +291,13 @@ int afc_set_dirichlet(afc_problem p, const uint8_t* mask, const double* values) 
   if (!mask || !values) { set_error("need mask and values"); return AFC_E_INVALID; }
   std::vector<uint8_t> m(mask, mask + p->N);
   for (auto& v : m) v = v ? 1 : 0;
+  p->dir_lo = 1e308;
+  p->dir_hi = -1e308;
+  for (int64_t i = 0; i < p->N; ++i)
+    if (m[i]) {
+      p->dir_lo = std::min(p->dir_lo, values[i]);
+      p->dir_hi = std::max(p->dir_hi, values[i]);
+    }
   AFC_CUDA(cudaMemcpyAsync(p->dir.p, m.data(), p->N, cudaMemcpyHostToDevice, p->stream));
   if ((st = to_device(p, p->udir.p, values, p->N))) return st;
   if ((st = sync(p))) return st;
@@ -392,6 +402,7 @@ int afc_set_solution(afc_problem p, const double* u, int is_device) {
   if (!u) { set_error("null argument"); return AFC_E_INVALID; }
   AFC_CUDA(cudaMemcpyAsync(p->u.p, u, p->N * sizeof(double),
                            is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+  p->u_range_valid = false;   // measured on the device by the next step or solve
   return sync(p);
 }
 
@@ -417,7 +428,8 @@ int afc_cfl_timestep(afc_problem p, double cfl, double* dt) {
   return AFC_OK;
 }
 
-int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
+namespace {
+int step_impl(afc_problem p, const afc_opts* o, afc_stats* stt) {
   int st = check(p, true);
   if (st) return st;
   if (!o || !(o->dt > 0.0)) { set_error("need options with dt > 0"); return AFC_E_INVALID; }
@@ -502,7 +514,7 @@ int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
   return finish_stats(p, stt, st);
 }
 
-int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
+int stationary_impl(afc_problem p, const afc_opts* o, afc_stats* stt) {
   int st = check(p, true);
   if (st) return st;
   if (!o) { set_error("null options"); return AFC_E_INVALID; }
@@ -520,10 +532,64 @@ int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
   AFC_LAUNCH(p, "k_apply_dirichlet", k_apply_dirichlet<<<grid_for(p->N), kBlock, 0, p->stream>>>(p->N, p->dir.p, p->udir.p, p->u.p));
   AFC_CUDA(cudaGetLastError());
   st = fixed_point(
-      p, o, 0, stt, [&]() { return mc_limited_residual(p, p->u.p, lim, p->res.p, p->scal.p); },
+      p, o, 0, stt, [&]() {
+        return mc_limited_residual(p, p->u.p, lim, p->res.p, p->scal.p, false, o->precision == AFC_MIXED);
+      },
       [&]() { return axpy_device(p, o->omega, p->delta.p, p->u.p); });
   if (st < 0) return st;
   return finish_stats(p, stt, st);
+}
+
+// Range of the stored solution before a call (computed on the device only when no
+// earlier call left it known).
+int input_range(afc_problem_s* p, double* lo, double* hi) {
+  if (!p->u_range_valid) {
+    int st = minmax_device(p, p->u.p, &p->u_lo, &p->u_hi);
+    if (st) return st;
+    p->u_range_valid = true;
+  }
+  *lo = std::min(p->u_lo, p->dir_lo);
+  *hi = std::max(p->u_hi, p->dir_hi);
+  return AFC_OK;
+}
+
+// dmp_violation and t_ms of a step or solve; the returned solution's range becomes the
+// next call's input range (not after an error: the state may then not be an iterate)
+int finish_call(afc_problem_s* p, afc_stats* stt, int status, double lo, double hi,
+                std::chrono::steady_clock::time_point t0) {
+  if (status < 0) {
+    p->u_range_valid = false;
+    return status;
+  }
+  stt->dmp_violation = std::max(0.0, std::max(lo - stt->umin, stt->umax - hi));
+  stt->t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  p->u_lo = stt->umin;
+  p->u_hi = stt->umax;
+  p->u_range_valid = true;
+  return status;
+}
+}  // namespace
+
+int afc_step(afc_problem p, const afc_opts* o, afc_stats* stt) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int st = check(p, true);
+  if (st) return st;
+  double lo, hi;
+  if ((st = input_range(p, &lo, &hi))) return st;
+  afc_stats local;
+  afc_stats* s = stt ? stt : &local;
+  return finish_call(p, s, step_impl(p, o, s), lo, hi, t0);
+}
+
+int afc_solve_stationary(afc_problem p, const afc_opts* o, afc_stats* stt) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int st = check(p, true);
+  if (st) return st;
+  double lo, hi;
+  if ((st = input_range(p, &lo, &hi))) return st;
+  afc_stats local;
+  afc_stats* s = stt ? stt : &local;
+  return finish_call(p, s, stationary_impl(p, o, s), lo, hi, t0);
 }
 
 int afc_fe_stage(afc_problem p, double dt, int limiter, double* u_tilde, double* Rp, double* Rm, double* Fstar,
@@ -583,7 +649,7 @@ int afc_mc_residual_sweep(afc_problem p, int limiter) {
     return AFC_E_INVALID;
   }
   if (p->family != AFC_FAMILY_MC && limiter != AFC_LIM_NONE) { set_error("needs the MC family"); return AFC_E_STATE; }
-  return mc_limited_residual(p, p->u.p, limiter, p->res.p, p->scal.p);
+  return mc_limited_residual(p, p->u.p, limiter, p->res.p, p->scal.p, false, true);
 }
 
 int afc_get_residual(afc_problem p, double* res) {

@@ -287,6 +287,7 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
     AFC_LAUNCH(p, "k_mc_extras", k_mc_extras<<<g, kBlock, 0, s>>>(N, p->offs, p->eps, p->c, p->mask.p, p->Kfull.p,
                                                                    p->Sfull.p, p->mL.p, p->d_up.p, p->kij_up.p,
                                                                    p->kji_up.p, p->d2_up.p, p->pairf.p, p->AG.p));
+    if (precision == AFC_MIXED && (st = mc_pair_setup(p))) return st;
   }
   // symmetric mass data of the upper half: m_up[ku][i] = m_{i, i + o}
   for (int ku = 0; ku < Kup; ++ku)

@@ -492,25 +492,58 @@ int run_steps(afc_batch_s* b, const afc_opts* o, const double* dt, int nsteps, c
   return AFC_OK;
 }
 
-int batch_status(afc_batch_s* b, afc_stats* stats, int stages) {
+// Extremes of every instance's stored solution (one launch), into b->mm_h.
+int batch_minmax(afc_batch_s* b) {
   const int n = (int)b->list.size();
   k_batch_minmax<<<n, 256, 0, b->stream>>>(b->tab_d, b->mm_d);
   b->launches++;
   AFC_CUDA(cudaGetLastError());
   AFC_CUDA(cudaMemcpyAsync(b->mm_h, b->mm_d, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  return AFC_OK;
+}
+
+// The instances' input ranges for afc_stats.dmp_violation: measured once for all when
+// any instance's range is not known from an earlier call.
+int batch_input_ranges(afc_batch_s* b) {
+  bool all = true;
+  for (auto* p : b->list) all = all && p->u_range_valid;
+  if (all) return AFC_OK;
+  int st = batch_minmax(b);
+  if (st) return st;
+  AFC_CUDA(cudaStreamSynchronize(b->stream));
+  for (size_t q = 0; q < b->list.size(); ++q) {
+    b->list[q]->u_lo = b->mm_h[2 * q];
+    b->list[q]->u_hi = b->mm_h[2 * q + 1];
+    b->list[q]->u_range_valid = true;
+  }
+  return AFC_OK;
+}
+
+int batch_status(afc_batch_s* b, afc_stats* stats, int stages) {
+  const int n = (int)b->list.size();
+  int st0 = batch_minmax(b);
+  if (st0) return st0;
   AFC_CUDA(cudaMemcpyAsync(b->mm_h + 2 * n, &b->bar->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   AFC_CUDA(cudaStreamSynchronize(b->stream));
   int err = 0;
   std::memcpy(&err, b->mm_h + 2 * n, sizeof(int));
   const int status = err ? AFC_E_TIMEOUT : AFC_OK;
-  if (stats)
-    for (int q = 0; q < n; ++q) {
+  for (int q = 0; q < n; ++q) {
+    afc_problem_s* p = b->list[q];
+    const double mn = b->mm_h[2 * q], mx = b->mm_h[2 * q + 1];
+    if (stats) {
+      const double lo = std::min(p->u_lo, p->dir_lo), hi = std::max(p->u_hi, p->dir_hi);
       std::memset(&stats[q], 0, sizeof(afc_stats));
       stats[q].stages = stages;
-      stats[q].umin = b->mm_h[2 * q];
-      stats[q].umax = b->mm_h[2 * q + 1];
+      stats[q].umin = mn;
+      stats[q].umax = mx;
+      stats[q].dmp_violation = std::max(0.0, std::max(lo - mn, mx - hi));
       stats[q].status = status;
     }
+    p->u_lo = mn;
+    p->u_hi = mx;
+    p->u_range_valid = !err;
+  }
   if (err) {
     AFC_CUDA(cudaMemsetAsync(b->bar, 0, sizeof(GridBar), b->stream));
     AFC_CUDA(cudaStreamSynchronize(b->stream));
@@ -613,6 +646,7 @@ extern "C" int afc_batch_step(afc_batch b, const afc_opts* o, const double* dt, 
   if (nsteps < 0) { set_error("nsteps must be >= 0"); return AFC_E_INVALID; }
   if (cudaSetDevice(b->device) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
   const afc_batch_tuning t = effective_tuning(b, o);
+  if ((st = batch_input_ranges(b))) return st;
   if ((st = run_steps(b, o, dt, nsteps, t))) return st;
   return batch_status(b, stats, nsteps * (o->scheme == AFC_SSP2 ? 2 : 3));
 }
@@ -700,6 +734,7 @@ extern "C" int afc_batch_tune(afc_batch b, const afc_opts* o, const double* dt, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   int st2 = copy_all(false);
+  for (auto* p : b->list) p->u_range_valid = false;   // the trials' ranges are not the restored states'
   if (st) return st;
   if (st2) return st2;
   AFC_CUDA(cudaStreamSynchronize(s));

@@ -392,7 +392,9 @@ int stationary_graph(afc_problem_s* p, const afc_opts* o, afc_stats* stt) {
           AFC_CUDA(cudaGetLastError());
           return AFC_OK;
         },
-        [&]() -> int { return mc_limited_residual(p, p->u.p, lim, p->res.p, nullptr); },
+        [&]() -> int {
+          return mc_limited_residual(p, p->u.p, lim, p->res.p, nullptr, false, o->precision == AFC_MIXED);
+        },
         [&]() -> int { return axpy_device(p, o->omega, p->delta.p, p->u.p); }, *p->g_stat);
     if (st) {
       drop(p->g_stat);

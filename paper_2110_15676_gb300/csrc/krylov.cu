@@ -57,6 +57,7 @@ template struct DBuf<int32_t>;
 template struct DBuf<uint8_t>;
 template struct DBuf<unsigned long long>;
 template struct DBuf<float4>;
+template struct DBuf<float2>;
 
 namespace {
 

@@ -352,7 +352,9 @@ int mc_ssp_fluxes(afc_problem_s* p, const double* u) {
 }
 
 int mc_limited_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot,
-                        bool want_F) {
+                        bool want_F, bool pair) {
+  if (pair && p->precision == AFC_MIXED && !want_F && (limiter == AFC_LIM_MC || limiter == AFC_LIM_GALERKIN))
+    return mc_pair_residual(p, u, limiter, res, normsq_slot);
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;

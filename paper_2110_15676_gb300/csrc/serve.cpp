@@ -2,15 +2,17 @@
 // concurrent stationary solves, admission by a device-memory budget.
 //
 // Threads.
-//  * admission: takes submitted requests in arrival order, waits until the
-//    budget and the slot count allow one more, builds its problem (mesh,
-//    coefficients, Dirichlet data, assembly, initial data) on the request's own
-//    stream, and hands it to the stepper (transient) or to the stationary queue.
+//  * admission (`builders` threads): take submitted requests in arrival order,
+//    each as soon as the budget and the slot count allow one more, build its
+//    problem (mesh, coefficients, Dirichlet data, assembly, initial data) on the
+//    request's own stream, and hand it to the stepper (transient) or to the
+//    stationary queue.  Several requests build at once, so that requests that
+//    arrive close together reach the stepper close together and join one batch.
 //  * stepper: keeps every admitted transient request resident on the device and
 //    advances all of them together, one batched SSP step sequence (a "chunk" of
-//    at most max_chunk steps) at a time; requests admitted meanwhile join at the
-//    next chunk boundary, finished ones leave (their solution is copied to the
-//    host and their device memory released).
+//    at most max_chunk steps) at a time, on a stream of the highest priority;
+//    requests admitted meanwhile join at the next chunk boundary, finished ones
+//    leave (their solution is copied to the host and their device memory released).
 //  * stationary workers: each runs one damped fixed-point solve at a time on the
 //    request's own stream, so several solves and the transient batch overlap on
 //    the device.
@@ -90,7 +92,7 @@ struct afc_server_s {
   std::map<int64_t, afc::ReqPtr> all;    // every request not yet released
   int active = 0;                        // admitted and not finished
   int64_t bytes_in_use = 0;
-  int64_t completed = 0, failed = 0, chunks = 0, batched_steps = 0;
+  int64_t completed = 0, failed = 0, chunks = 0, batched_steps = 0, instance_steps = 0;
   int64_t max_batch = 0;
   std::vector<std::thread> threads;
 };
@@ -210,9 +212,9 @@ void admission_loop(afc_server_s* s) {
         s->cv_admit.wait(lk);
       }
     }
-    int st = build_problem(s, *r);
-    if (st) {
-      finish(s, r, AFC_REQ_FAILED, st);
+    int st = r->cancel ? AFC_OK : build_problem(s, *r);
+    if (st || r->cancel) {
+      finish(s, r, st ? AFC_REQ_FAILED : AFC_REQ_CANCELLED, st);
       continue;
     }
     std::lock_guard<std::mutex> lk(s->mu);
@@ -257,8 +259,14 @@ std::string group_key(const afc_request& q) {
 
 void stepper_loop(afc_server_s* s) {
   cudaSetDevice(s->device);
+  // The batch runs at the highest stream priority: a chunk of batched steps is short
+  // work that many requests wait on, so its kernels go ahead of the long stationary
+  // solves (on default-priority streams) whenever both are queued on the device.
   cudaStream_t ws = nullptr;
-  cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ws, cudaStreamNonBlocking, greatest) != cudaSuccess)
+    cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
   std::map<std::string, Group> groups;
   std::vector<afc_stats> stats;
   std::vector<double> dts;
@@ -318,6 +326,7 @@ void stepper_loop(afc_server_s* s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->chunks++;
         s->batched_steps += chunk;
+        s->instance_steps += chunk * (int64_t)g.members.size();
       }
       std::vector<ReqPtr> keep;
       for (size_t q = 0; q < g.members.size(); ++q) {
@@ -327,12 +336,14 @@ void stepper_loop(afc_server_s* s) {
           finish(s, r, AFC_REQ_FAILED, st);
         } else if (r->steps_left <= 0) {
           r->stats.stages += stats[q].stages;
+          r->stats.dmp_violation = std::max(r->stats.dmp_violation, stats[q].dmp_violation);
           r->stats.umin = stats[q].umin;
           r->stats.umax = stats[q].umax;
           r->stats.status = AFC_OK;
           finish(s, r, AFC_REQ_DONE, AFC_OK);
         } else {
           r->stats.stages += stats[q].stages;
+          r->stats.dmp_violation = std::max(r->stats.dmp_violation, stats[q].dmp_violation);
           keep.push_back(r);
         }
       }
@@ -380,6 +391,7 @@ void serial_loop(afc_server_s* s) {
         for (int k = 0; k < r->spec.steps && st >= 0; ++k) {
           st = afc_step(r->p, &o, &one);
           r->stats.stages += one.stages;
+          r->stats.dmp_violation = std::max(r->stats.dmp_violation, one.dmp_violation);
         }
         r->stats.umin = one.umin;
         r->stats.umax = one.umax;
@@ -422,6 +434,7 @@ extern "C" void afc_serve_default_config(afc_serve_config* c) {
   c->hbm_budget = (int64_t)64 << 30;
   c->stationary_workers = 4;
   c->max_chunk = 10;
+  c->builders = 4;
 }
 
 extern "C" int64_t afc_serve_estimate_bytes(const afc_request* r) {
@@ -436,7 +449,8 @@ extern "C" int afc_serve_create(int device, const afc_serve_config* cfg, afc_ser
   afc_serve_default_config(&c);
   if (cfg) c = *cfg;
   if ((c.mode != AFC_SERVE_BATCHED && c.mode != AFC_SERVE_SERIAL) || c.max_active < 1 || c.hbm_budget <= 0 ||
-      c.stationary_workers < 1 || c.stationary_workers > 64 || c.max_chunk < 1) {
+      c.stationary_workers < 1 || c.stationary_workers > 64 || c.max_chunk < 1 || c.builders < 1 ||
+      c.builders > 64) {
     set_error("bad server configuration");
     return AFC_E_INVALID;
   }
@@ -448,7 +462,7 @@ extern "C" int afc_serve_create(int device, const afc_serve_config* cfg, afc_ser
   if (c.mode == AFC_SERVE_SERIAL) {
     s->threads.emplace_back(serial_loop, s);
   } else {
-    s->threads.emplace_back(admission_loop, s);
+    for (int w = 0; w < c.builders; ++w) s->threads.emplace_back(admission_loop, s);
     s->threads.emplace_back(stepper_loop, s);
     for (int w = 0; w < c.stationary_workers; ++w) s->threads.emplace_back(stationary_loop, s);
   }
@@ -564,6 +578,7 @@ extern "C" int afc_serve_get_info(afc_server s, afc_serve_info* out) {
   out->chunks = s->chunks;
   out->batched_steps = s->batched_steps;
   out->max_batch = s->max_batch;
+  out->instance_steps = s->instance_steps;
   out->clock = now_s(s);
   return AFC_OK;
 }

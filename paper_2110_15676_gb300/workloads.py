@@ -17,6 +17,9 @@ constant convection, small diffusion, data in [0, 1]):
   z = 0 with value 1 where x = 0 and y < 0.5, else 0.
 * ``random_transient``: a seeded random instance (node count per side, eps,
   constant unit velocity, hump centre) for batched runs.
+* ``rotating_shapes``: the paper's rotating-shapes example (eps = 0, the same
+  rotating field, initial data 1 inside a cube, a cone and a hollow cylinder and 0
+  elsewhere, ``rotating_bodies``), homogeneous Dirichlet data on the boundary.
 * ``circular_convection``: the paper's circular convection example (eps = 0,
   b = (y, -x, 0), exact solution ``circular_exact`` as Dirichlet data on the
   faces y = 1, x = 0, x = 1) on the Kuhn P1 grid.
@@ -94,6 +97,42 @@ def rotating_transient(elem: str, n: int, eps: float = 1e-6) -> Workload:
     return Workload(
         name=f"rotating_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
         eps=eps, c=0.0, b=rotating_b(xyz), f=np.zeros(N), u0=cosine_hump(xyz),
+        dir_mask=boundary_mask(n), u_dir=np.zeros(N))
+
+
+def rotating_bodies(x, y, z) -> np.ndarray:
+    """Indicator (1 inside or on the surface, else 0) of the three bodies of the
+    rotating-shapes example: the cube of edge 0.25 centred at (0.5, 0.25, 0.5); the
+    cone of height 0.5 over the disc of radius 0.125 centred at (0.75, 0.5, 0.25) in
+    the plane z = 0.25; the hollow cylinder of inner radius 0.0625, outer radius
+    0.125 and height 0.5 over the centre (0.5, 0.75, 0.25)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    cube = (np.abs(x - 0.5) <= 0.125) & (np.abs(y - 0.25) <= 0.125) & (np.abs(z - 0.5) <= 0.125)
+    zc = (z >= 0.25) & (z <= 0.75)
+    rc = np.hypot(x - 0.75, y - 0.5)
+    cone = zc & (rc <= 0.125 * (1.0 - (z - 0.25) / 0.5))
+    rh = np.hypot(x - 0.5, y - 0.75)
+    hollow = zc & (rh >= 0.0625) & (rh <= 0.125)
+    return (cube | cone | hollow).astype(np.float64)
+
+
+# bounding box of the three bodies, and their total volume:
+# 0.25^3 + pi 0.125^2 0.5 / 3 + pi (0.125^2 - 0.0625^2) 0.5
+ROTATING_BODIES_BOX = ((0.375, 0.875), (0.125, 0.875), (0.25, 0.75))
+ROTATING_BODIES_VOLUME = 0.25 ** 3 + np.pi * 0.125 ** 2 * 0.5 / 3.0 + np.pi * (0.125 ** 2 - 0.0625 ** 2) * 0.5
+
+
+def rotating_shapes(elem: str, n: int) -> Workload:
+    """The rotating-shapes example: unit cube, eps = 0, b = (0.5 - y, x - 0.5, 0),
+    c = 0, f = 0, u_D = 0 on the whole boundary, u0 the bodies' indicator at the
+    nodes.  One rotation takes t = 2 pi, after which the exact solution is u0 again."""
+    xyz = grid_coords(n)
+    N = len(xyz)
+    return Workload(
+        name=f"rotating_shapes_{elem}_{n}^3", elem=elem, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
+        eps=0.0, c=0.0, b=rotating_b(xyz), f=np.zeros(N), u0=rotating_bodies(xyz[:, 0], xyz[:, 1], xyz[:, 2]),
         dir_mask=boundary_mask(n), u_dir=np.zeros(N))
 
 

@@ -157,6 +157,7 @@ def test_cn_step_full_size_q1_65_matches_oracle(afc):
     o = O.assemble(mesh, wl.eps, wl.b, wl.c, wl.f, wl.dir_mask.astype(bool), wl.u_dir)
     dt = O.cfl_timestep(o, 1.0)
     u_ref, sto = O.cn_step(o, wl.u0, dt, fixed_iterations=6, ksp_atol=1e-14)
+    assert np.isfinite(u_ref).all()
     P = afc.Problem.structured(wl.elem, wl.n)
     P.set_coefficients(wl.eps, wl.b, wl.c, wl.f)
     P.set_dirichlet(wl.dir_mask, wl.u_dir)
@@ -168,5 +169,6 @@ def test_cn_step_full_size_q1_65_matches_oracle(afc):
                                      graph=graph))
         assert st["outer_its"] == 6 == sto["outer_its"]
         u = P.get_solution()
+        assert np.isfinite(u).all(), (graph, np.flatnonzero(~np.isfinite(u))[:8])
         err = np.abs(u - u_ref).max() / np.abs(u_ref).max()
         assert err <= 1e-10, (graph, err)

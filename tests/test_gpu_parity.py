@@ -377,15 +377,83 @@ def test_stationary_bicgstab_and_not_converged_status(afc):
 
 
 @pytest.mark.parametrize("elem", ["p1", "q1"])
-def test_mc_stationary_mixed_precision(afc, elem):
+@pytest.mark.parametrize("graph", [1, 0])
+def test_mc_stationary_mixed_precision(afc, elem, graph):
+    """FP32 inner GMRES, float-pair residual and clip: the converged solution within
+    1e-6 of the FP64 oracle's, inside [0, 1] up to the solver tolerance."""
     wl = W.stationary_inflow(elem, 9)
     o, g = pair_from_workload(wl, "mc", precision="mixed")
     u_ref, _ = O.mc_stationary(o, tol=1e-10, omega=0.5, ksp="gmres", ksp_atol=1e-14, max_outer=1000)
     g.set_solution(wl.u0)
     st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, fp_tol=1e-10, omega=0.5, ksp=afc.AFC_KSP_GMRES,
-                                             ksp_atol=0.0, ksp_rtol=1e-6, fp_maxit=1000, precision=afc.AFC_MIXED))
+                                             ksp_atol=0.0, ksp_rtol=1e-6, fp_maxit=1000, precision=afc.AFC_MIXED,
+                                             graph=graph))
     assert st["status"] == afc.AFC_OK
-    assert relerr(g.get_solution(), u_ref) < 1e-6
+    ug = g.get_solution()
+    assert relerr(ug, u_ref) < 1e-6
+    assert ug.min() >= -1e-10 and ug.max() <= 1 + 1e-10
+
+
+def _pair_sweep_field(kind, o, wl, rng):
+    N = o.mesh.n_nodes
+    if kind == "uniform":
+        u = rng.uniform(0, 1, N)
+    elif kind == "front":
+        u = W.front_field(o.mesh.xyz, rng)
+    elif kind == "exact_floats":      # every value a float: the pairs' low parts are 0
+        u = np.float32(rng.uniform(0, 1, N)).astype(np.float64)
+        u[1::2] = u[0::2][: len(u[1::2])]                      # many equal neighbours
+    else:                             # "wide": magnitudes over 70 decades, both signs
+        u = rng.choice([-1.0, 1.0], N) * rng.uniform(1, 10, N) * 10.0 ** rng.uniform(-35, 35, N)
+    u[o.dir_mask] = o.u_dir[o.dir_mask]
+    return u
+
+
+@pytest.mark.parametrize("elem,n", [("p1", 9), ("q1", (8, 7, 6)), ("p1", (17, 12, 10))])
+@pytest.mark.parametrize("field", ["uniform", "front", "exact_floats", "wide"])
+@pytest.mark.parametrize("limiter", ["mc", "galerkin"])
+def test_mc_pair_sweep_parity(afc, elem, n, field, limiter):
+    """The mixed-precision sweep (float-pair residual and clip, mc_pair.cu) against the
+    oracle's residual f + F*(u) - AA u (Sec. 4, Eq. MClimiter), row by row, 0 on
+    Dirichlet rows, and against the FP64 sweep of the same problem.  The bound is
+    1e-13 of the magnitudes that enter row i (plus 1e-36 absolute, below which float
+    pairs hold no digits): |f_i|, |AA_ij u_j|, and for each pair the terms of its two
+    clip tests, 2|d_ij| times the bounds of both ends (which reach the neighbours of
+    j) and |k_ij|, |k_ji| times |u_i| + |u_j|.  On the O(1) fields that is the row's
+    scale; on the field spanning 70 decades it is what a rounding of the clip tests'
+    terms can change, in FP64 as in float pairs."""
+    wl = random_workload(elem, n, seed=23)
+    o, g = pair_from_workload(wl, "mc", precision="mixed")
+    rng = np.random.default_rng({"uniform": 1, "front": 2, "exact_floats": 3, "wide": 4}[field])
+    u = _pair_sweep_field(field, o, wl, rng)
+    lm = afc.AFC_LIM_MC if limiter == "mc" else afc.AFC_LIM_GALERKIN
+    g.set_solution(u)
+    g.mc_residual_sweep(lm)
+    res = g.get_residual()
+    rstar, _ = O.mc_limited_fluxes(o, u, limiter)
+    F = O.limited_sum(o, np.ones_like(rstar), rstar)
+    ro = o.f + F - o.AA @ u
+    ro[o.dir_mask] = 0.0
+    I, J = o.pairs
+    umax, umin = O.mc_bounds(o, u)
+    bnd = np.abs(umax) + np.abs(umin)
+    d = np.abs(O.entries(o.D, I, J))
+    kk = np.abs(O.entries(o.K, I, J)) + np.abs(O.entries(o.K, J, I))
+    terms = np.abs(rstar) + 2.0 * d * (bnd[I] + bnd[J]) + kk * (np.abs(u[I]) + np.abs(u[J]))
+    rabs = np.zeros(o.mesh.n_nodes)
+    np.add.at(rabs, I, terms if limiter == "mc" else np.abs(rstar))
+    scale = np.abs(o.f) + abs(o.AA) @ np.abs(u) + rabs
+    assert (res[o.dir_mask] == 0).all()
+    free = ~o.dir_mask
+    assert (np.abs(res - ro)[free] <= PASS_TOL * scale[free] + 1e-36).all()
+    # the FP64 sweep of the same problem
+    g64 = gpu_problem(wl.elem, wl.n, wl.b, wl.eps, wl.c, wl.f, wl.dir_mask, wl.u_dir, "mc", "fp64", wl.lo, wl.hi)
+    g64.set_solution(u)
+    g64.mc_residual_sweep(lm)
+    r64 = g64.get_residual()
+    assert (np.abs(res - r64)[free] <= PASS_TOL * scale[free] + 1e-36).all()
+    g.close()
+    g64.close()
 
 
 # ------------------------------------------------------------------ Krylov and SpMV
@@ -440,3 +508,34 @@ def test_errors_reported(afc):
     g.set_dirichlet(np.ones(g.N, np.uint8), np.zeros(g.N))
     with pytest.raises(afc.AfcError):
         g.cfl_timestep(0.5)                             # no free node
+
+
+# ------------------------------------------------------------------ afc_stats: DMP and timing
+def test_dmp_violation_and_call_time_reported(afc):
+    """afc_stats.dmp_violation = max(0, lo - umin, umax - hi), [lo, hi] the range of the
+    call's input state and of the Dirichlet values: at rounding level for Zalesak's
+    limiter on discontinuous data (Sec. 2.1.3: the limited stage stays in the local
+    bounds), clearly positive for the unlimited Galerkin stage (alpha = 1) on the same
+    data, and equal to its definition evaluated on the host from the states."""
+    wl = W.rotating_shapes("q1", 17)
+    g = gpu_problem(wl.elem, wl.n, wl.b, wl.eps, wl.c, wl.f, wl.dir_mask, wl.u_dir)
+    dm = wl.dir_mask.astype(bool)
+    dt = g.cfl_timestep(0.5)
+    for lim, small in ((afc.AFC_LIM_ZALESAK, True), (afc.AFC_LIM_GALERKIN, False)):
+        g.set_solution(wl.u0)
+        worst = 0.0
+        for step in range(6):
+            u_in = g.get_solution()
+            st = g.step(afc.default_opts(scheme=afc.AFC_SSP3, limiter=lim, dt=dt))
+            u_out = g.get_solution()
+            lo = min(u_in.min(), wl.u_dir[dm].min())
+            hi = max(u_in.max(), wl.u_dir[dm].max())
+            ref = max(0.0, lo - u_out.min(), u_out.max() - hi)
+            assert abs(st["dmp_violation"] - ref) <= 1e-15 * max(1.0, ref)
+            assert st["t_ms"] > 0.0
+            worst = max(worst, st["dmp_violation"])
+        if small:
+            assert worst <= 1e-14
+        else:
+            assert worst > 1e-3
+    g.close()

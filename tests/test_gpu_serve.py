@@ -144,3 +144,52 @@ def test_cancel_timeout_and_errors(afc):
         with pytest.raises(afc.AfcError) as e:
             small.submit(reqs[0])
         assert e.value.status == afc.AFC_E_INVALID
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_served_results_match_the_oracle(afc, prec):
+    """Every request of a served mix against the CPU oracle: transient requests
+    against the oracle's SSP3 Zalesak steps, stationary ones against its damped MC
+    fixed point (Sec. 3.1, Sec. 4) converged with exact inner solves.  FP64 requests
+    (stationary fixed point to 1e-12, inner GMRES to 1e-14) within 1e-10 relative
+    max-norm; mixed requests (FP32 fluxes or inner solves, float-pair MC residual,
+    fixed point to 1e-10) within 1e-6."""
+    from oracle import afc_oracle as O
+    p = afc.AFC_MIXED if prec == "mixed" else afc.AFC_FP64
+    tol = 1e-6 if prec == "mixed" else 1e-10
+    mix = W.serving_mix(np.random.default_rng(55), 8, n_range=(6, 10))
+
+    def sopts():
+        if prec == "mixed":
+            return afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
+                                    ksp_rtol=1e-6, fp_tol=1e-10, fp_maxit=1000, precision=p)
+        return afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=1e-14,
+                                fp_tol=1e-12, fp_maxit=2000, precision=p)
+
+    with afc.Server(stationary_workers=3, max_chunk=3, builders=3) as srv:
+        ids = []
+        for kind, wl in mix:
+            k = afc.AFC_REQ_TRANSIENT if kind == "transient" else afc.AFC_REQ_STATIONARY
+            o = opts_for(afc, kind, p) if kind == "transient" else sopts()
+            ids.append(srv.submit(afc.Request(k, wl.elem, wl.n, wl.eps, wl.c, wl.b, wl.u0, wl.dir_mask, wl.u_dir,
+                                              f=wl.f, opts=o, steps=STEPS, cfl=0.5)))
+        got = []
+        for rid in ids:
+            res, u = srv.wait(rid, timeout=300.0)
+            assert res["state"] == afc.AFC_REQ_DONE and res["status"] == afc.AFC_OK, res
+            got.append(u)
+            srv.release(rid)
+    for (kind, wl), u in zip(mix, got):
+        mesh = O.structured_mesh(wl.elem, wl.n)
+        fam = "fct" if kind == "transient" else "mc"
+        o = O.assemble(mesh, wl.eps, wl.b, wl.c, wl.f, wl.dir_mask.astype(bool), wl.u_dir, fam)
+        if kind == "transient":
+            dt = O.cfl_timestep(o, 0.5)
+            ref = wl.u0.copy()
+            for _ in range(STEPS):
+                ref = O.ssp_step(o, ref, dt, order=3)
+        else:
+            ref, st = O.mc_stationary(o, u0=wl.u0, tol=1e-12, omega=0.5, ksp="direct", max_outer=4000)
+            assert st["converged"]
+        err = np.abs(u - ref).max() / max(np.abs(ref).max(), 1e-300)
+        assert err <= tol, (kind, wl.name, err)

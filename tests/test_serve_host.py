@@ -34,9 +34,9 @@ def test_estimate_grows_with_size_and_pattern(afc):
 
 def test_bad_server_configurations_are_rejected_on_the_host(afc):
     for kw in ({"mode": 7}, {"max_active": 0}, {"hbm_budget": 0}, {"stationary_workers": 0},
-               {"stationary_workers": 65}, {"max_chunk": 0}):
+               {"stationary_workers": 65}, {"max_chunk": 0}, {"builders": 0}, {"builders": 65}):
         with pytest.raises(afc.AfcError) as e:
             afc.Server(**kw)
         assert e.value.status == afc.AFC_E_INVALID
     c = afc.serve_config()
-    assert c.mode == afc.AFC_SERVE_BATCHED and c.max_chunk >= 1 and c.hbm_budget > 0
+    assert c.mode == afc.AFC_SERVE_BATCHED and c.max_chunk >= 1 and c.hbm_budget > 0 and c.builders >= 1
