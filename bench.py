@@ -207,14 +207,15 @@ def _roofline(name, kms, kcount, work_flops, share):
             "avg_launch_us": kms / kcount * 1e3, "share": share}
 
 
-def _mc_solve(afc, P, wl, torch, stream):
+def _mc_solve(afc, P, wl, torch, stream, rtol=1e-6, ref=None, sweep_ms=None):
     # the whole stationary MC solve of this workload (damped fixed point, omega = 0.5,
-    # tol 1e-10, mixed-precision Jacobi-GMRES(20) inner solves to a relative 1e-6)
-    sopts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0, ksp_rtol=1e-6,
+    # tol 1e-10, mixed-precision Jacobi-GMRES(20) inner solves to a relative rtol);
+    # with ref, also the largest difference from that solution relative to its maximum
+    sopts = afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0, ksp_rtol=rtol,
                              fp_tol=1e-10, fp_maxit=1000, precision=afc.AFC_MIXED)
     P.set_solution(wl.u0)
     P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
-                                        ksp_rtol=1e-6, fp_fixed_its=1, precision=afc.AFC_MIXED))   # build / warm
+                                        ksp_rtol=rtol, fp_fixed_its=1, precision=afc.AFC_MIXED))   # build / warm
     P.set_solution(wl.u0)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -226,14 +227,34 @@ def _mc_solve(afc, P, wl, torch, stream):
     solve_ms = e0.elapsed_time(e1)
     u_sol = P.get_solution()
     N = P.info()["n_nodes"]
-    return {"ms": solve_ms, "fixed_point_its": sst["outer_its"], "gmres_its": sst["inner_its"],
-            "status": sst["status"], "res_final": sst["res_final"],
-            "dof_iters_per_s": N * sst["outer_its"] / (solve_ms / 1e3),
-            "umin": float(u_sol.min()), "umax": float(u_sol.max()),
-            "options": "omega 0.5, tol 1e-10, mixed: FP32 Jacobi-GMRES(20) rtol 1e-6, FP64 outer"}
+    out = {"ms": solve_ms, "fixed_point_its": sst["outer_its"], "gmres_its": sst["inner_its"],
+           "status": sst["status"], "res_final": sst["res_final"],
+           "dof_iters_per_s": N * sst["outer_its"] / (solve_ms / 1e3),
+           "umin": float(u_sol.min()), "umax": float(u_sol.max()), "dmp_violation": sst["dmp_violation"],
+           "options": f"omega 0.5, tol 1e-10, mixed: FP32 Jacobi-GMRES(20) rtol {rtol:g}, float-pair MC residual, "
+                      f"FP64 outer"}
+    if ref is not None:
+        out["rel_diff_vs_rtol_1e-6"] = float(np.abs(u_sol - ref).max() / np.abs(ref).max())
+    if sweep_ms is not None and sst["inner_its"] > 0:
+        # the inner solves' share: the solve's time without its residual sweeps (one per
+        # fixed-point iteration and a final one), per GMRES iteration, against the
+        # algorithmic bytes of one Arnoldi step with single-precision vectors: the product
+        # (CSR count, 8 nnz + 12 N) and classical Gram-Schmidt without the
+        # re-orthogonalisation pass over the average k + 1 = 10.5 basis vectors of
+        # GMRES(20) (4 N (2 k + 5)) plus the normalisation (16 N): 8 nnz + 132 N
+        info = P.info()
+        nnz = info["nnz"]
+        g_ms = solve_ms - (sst["outer_its"] + 1) * sweep_ms
+        per = g_ms / sst["inner_its"]
+        b = 8.0 * nnz + 132.0 * N
+        peaks, src = _peaks()
+        out["gmres"] = {"ms_per_iteration": per, "algorithmic_bytes_per_iteration": b,
+                        "achieved_gbs": b / (per / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                        "frac": b / (per / 1e3) / 1e9 / peaks["hbm_gbs"], "peak_source": src}
+    return out, u_sol
 
 
-def mc_sweep(afc, W, torch, flush, stream, reps, solve=True):
+def mc_sweep(afc, W, torch, flush, stream, reps, solve=True, inner_rtols=()):
     """The stationary MC limiter + residual sweep on Kuhn P1 129^3 (2,146,689 dofs):
     bounds, limited fluxes of all 14.8 M pairs, residual SpMV and norm, timed on the
     iterate after 6 damped fixed-point corrections from u0."""
@@ -271,8 +292,12 @@ def mc_sweep(afc, W, torch, flush, stream, reps, solve=True):
     P.profile(False)
     sweep_ms = ms / reps
     solve_out = None
+    inner = None
     if solve:
-        solve_out = _mc_solve(afc, P, wl, torch, stream)
+        solve_out, u_ref = _mc_solve(afc, P, wl, torch, stream, sweep_ms=ms / reps)
+        if inner_rtols:
+            inner = {f"{r:g}": _mc_solve(afc, P, wl, torch, stream, rtol=r, ref=u_ref, sweep_ms=ms / reps)[0]
+                     for r in inner_rtols}
     # algorithmic work of one sweep (design notes): FP64 flops 14 per pair + 2 per entry;
     # bytes of the CSR count 4(N+1) + 12 nnz + 24 E + 24 N
     flops = 14.0 * E + 2.0 * nnz
@@ -287,7 +312,7 @@ def mc_sweep(afc, W, torch, flush, stream, reps, solve=True):
                    "unit": "TFLOP/s", "frac": flops / (sweep_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                    "algorithmic_flops": flops},
            "kernels": {k: {"ms": v[0] / reps, "launches": v[1] // reps} for k, v in prof.items()},
-           "solve": solve_out}
+           "solve": solve_out, "inner_rtol_sweep": inner}
     del P
     return out
 
@@ -535,8 +560,9 @@ def run_ours(args, ws, rank, local):
         return
     if args.only_mc_sweep:
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        rt = tuple(float(x) for x in args.mc_inner_rtols.split(",")) if args.mc_inner_rtols else ()
         print(json.dumps({"mc_sweep": mc_sweep(afc, W, torch, flush, torch.cuda.current_stream(),
-                                               max(args.steps, 1), solve=not args.no_mc_solve)}))
+                                               max(args.steps, 1), solve=not args.no_mc_solve, inner_rtols=rt)}))
         return
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -804,6 +830,8 @@ def main():
     ap.add_argument("--batched-block", type=int, default=128)
     ap.add_argument("--no-solo", action="store_true", help="skip the one-at-a-time path (--only-batched)")
     ap.add_argument("--no-mc-solve", action="store_true", help="time the MC sweep but not the whole MC solve")
+    ap.add_argument("--mc-inner-rtols", default="", help="--only-mc-sweep: also solve with these inner GMRES "
+                                                          "tolerances (comma separated) and compare")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--only-serving", action="store_true", help="time only the request-server streams")
     ap.add_argument("--serving-count", type=int, default=48)

@@ -146,10 +146,19 @@ int afc_destroy(afc_problem p);
 
 /* ---- data --------------------------------------------------------------------- */
 
-/* Coefficients of Eq. tcdr / Eq. cdr: diffusion eps >= 0, nodal velocity
- * b_nodal[3*N] (interpolated with the element basis), constant reaction c >= 0,
- * nodal source f_nodal[N] (NULL = 0).  The load vector is M_L f_nodal. */
-int afc_set_coefficients(afc_problem p, double eps, const double* b_nodal, double c, const double* f_nodal);
+/* Coefficients of Eq. tcdr / Eq. cdr (host arrays):
+ *  eps       diffusion, >= 0;
+ *  b_nodal   velocity at the nodes, b_nodal[3*i + d] (interpolated with the element
+ *            basis), or NULL to use the constant b_const[3] at every node;
+ *  c_nodal   reaction at the nodes (N values >= 0, interpolated with the element
+ *            basis: the Galerkin matrix (c_h phi_j, phi_i), lumped to its row sums in
+ *            the MC family), or NULL for the constant c_const >= 0 (c_const M_C, and
+ *            c_const M_L in the MC family);
+ *  f_nodal   source at the nodes (NULL = 0); the load vector is M_L f_nodal.
+ * AFC_E_INVALID for a negative or non-finite eps or reaction, or neither b_nodal
+ * nor b_const.  The next afc_assemble uses them. */
+int afc_set_coefficients(afc_problem p, double eps, const double* b_nodal, const double b_const[3],
+                         const double* c_nodal, double c_const, const double* f_nodal);
 
 /* Dirichlet set: mask[N] (nonzero = Dirichlet node), values[N] (used where mask). */
 int afc_set_dirichlet(afc_problem p, const uint8_t* mask, const double* values);

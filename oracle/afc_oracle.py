@@ -126,7 +126,41 @@ def p1_element_matrices(X, B):
     return M, S, C
 
 
+def p1_reaction_matrix(X, Cn):
+    """(c_h phi_j, phi_i) for c_h = sum_k c_k lambda_k, exactly:
+    int lambda_i lambda_j lambda_k = V (1 + d_ij + d_ik + d_jk + 2 d_ijk) / 120
+    (the integral of a product of barycentric coordinates, 6 V a! b! c! d! / (a+b+c+d+3)!).
+    X: (E, 4, 3) vertices, Cn: (E, 4) nodal reaction.  Returns (E, 4, 4)."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 4, 3)
+    Cn = np.asarray(Cn, dtype=np.float64).reshape(-1, 4)
+    J = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], axis=2)
+    V = np.abs(np.linalg.det(J)) / 6.0
+    d = np.eye(4)
+    T = (1.0 + d[:, :, None] + d[:, None, :] + d[None, :, :] + 2.0 * np.einsum("ij,jk->ijk", d, d)) / 120.0
+    return V[:, None, None] * np.einsum("ijk,ek->eij", T, Cn)
+
+
 _GAUSS01 = (0.5 - 0.5 / math.sqrt(3.0), 0.5 + 0.5 / math.sqrt(3.0))
+
+
+def q1_reaction_matrix(X, Cn):
+    """(c_h phi_j, phi_i) for the trilinear interpolant c_h of the nodal reaction, by
+    2x2x2 Gauss quadrature (exact on parallelepipeds: the integrand has degree 3 in
+    each reference coordinate).  X: (E, 8, 3), Cn: (E, 8).  Returns (E, 8, 8)."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 8, 3)
+    Cn = np.asarray(Cn, dtype=np.float64).reshape(-1, 8)
+    R = np.zeros((X.shape[0], 8, 8))
+    bits = np.array([[k & 1, (k >> 1) & 1, (k >> 2) & 1] for k in range(8)], dtype=np.float64)
+    for xi in itertools.product(_GAUSS01, repeat=3):
+        f1 = [np.where(bits[:, d] == 1, xi[d], 1.0 - xi[d]) for d in range(3)]
+        df = [np.where(bits[:, d] == 1, 1.0, -1.0) for d in range(3)]
+        phi = f1[0] * f1[1] * f1[2]
+        dphi_ref = np.stack([df[0] * f1[1] * f1[2], f1[0] * df[1] * f1[2], f1[0] * f1[1] * df[2]], axis=1)
+        J = np.einsum("eka,kd->ead", X, dphi_ref)
+        wd = 0.125 * np.abs(np.linalg.det(J))
+        cq = Cn @ phi
+        R += (wd * cq)[:, None, None] * np.outer(phi, phi)[None]
+    return R
 
 
 def q1_element_matrices(X, B):
@@ -162,7 +196,7 @@ def q1_element_matrices(X, B):
 class Problem:
     mesh: Mesh
     eps: float
-    c: float
+    c: object                     # constant reaction (float) or nodal values (N,)
     b: np.ndarray                 # (N, 3) nodal velocity
     f_nodal: np.ndarray           # (N,)
     dir_mask: np.ndarray          # (N,) bool
@@ -181,7 +215,10 @@ class Problem:
     extra: dict = field(default_factory=dict)
 
 
-def assemble(mesh: Mesh, eps: float, b, c: float, f_nodal, dir_mask, u_dir, limiter_family="fct") -> Problem:
+def assemble(mesh: Mesh, eps: float, b, c, f_nodal, dir_mask, u_dir, limiter_family="fct") -> Problem:
+    """c: a constant reaction (float) or nodal values (N,), interpolated with the
+    element basis; the reaction term is the Galerkin matrix (c phi_j, phi_i) (= c M_C
+    for a constant), lumped to its row sums in the MC system (reading A9)."""
     N = mesh.n_nodes
     b = np.broadcast_to(np.asarray(b, dtype=np.float64), (N, 3)).copy()
     f_nodal = np.broadcast_to(np.asarray(f_nodal, dtype=np.float64), (N,)).copy()
@@ -203,8 +240,18 @@ def assemble(mesh: Mesh, eps: float, b, c: float, f_nodal, dir_mask, u_dir, limi
     pattern.data[:] = 1.0
     MC = _on_pattern(MC, pattern); S = _on_pattern(S, pattern); K = _on_pattern(K, pattern)
     mL = np.asarray(MC.sum(axis=1)).ravel()                   # m_i = sum_j m_ij
+    if np.ndim(c) == 0:
+        R = c * MC
+        rL = c * mL
+    else:
+        cn = np.broadcast_to(np.asarray(c, dtype=np.float64), (N,))
+        rmat = p1_reaction_matrix if mesh.elem == P1 else q1_reaction_matrix
+        R = sp.csr_matrix((rmat(mesh.xyz[cells], cn[cells]).ravel(), (rows, cols)), shape=(N, N))
+        R.sum_duplicates()
+        R = _on_pattern(R, pattern)
+        rL = np.asarray(R.sum(axis=1)).ravel()
     if limiter_family == "fct":
-        A = (eps * S + K + c * MC).tocsr()                    # a_ij of Sec. 2
+        A = (eps * S + K + R).tocsr()                         # a_ij of Sec. 2
         D = discrete_upwinding(A)
         AA = (A + D).tocsr()
     elif limiter_family == "mc":
@@ -212,7 +259,7 @@ def assemble(mesh: Mesh, eps: float, b, c: float, f_nodal, dir_mask, u_dir, limi
         # eps = 0, c = 0 operator, unlimited diffusion and (lumped) reaction.
         A = K.copy()
         D = discrete_upwinding(K)
-        AA = (K + D + eps * S + sp.diags(c * mL)).tocsr()
+        AA = (K + D + eps * S + sp.diags(rL)).tocsr()
     else:
         raise ValueError(limiter_family)
     AA = _on_pattern(AA, pattern)

@@ -99,7 +99,7 @@ _SIGS = {
     "afc_create_structured": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, _P, C.POINTER(_P)]),
     "afc_create_from_elements": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, C.c_int, _P, C.POINTER(_P)]),
     "afc_destroy": (C.c_int, [_P]),
-    "afc_set_coefficients": (C.c_int, [_P, C.c_double, _D, C.c_double, _D]),
+    "afc_set_coefficients": (C.c_int, [_P, C.c_double, _D, _D, _D, C.c_double, _D]),
     "afc_set_dirichlet": (C.c_int, [_P, _U8, _D]),
     "afc_assemble": (C.c_int, [_P, C.c_int, C.c_int]),
     "afc_get_info": (C.c_int, [_P, C.POINTER(afc_info)]),
@@ -284,10 +284,17 @@ class Problem:
 
     # ---- data ----
     def set_coefficients(self, eps, b, c=0.0, f=None):
-        b = _f64(np.broadcast_to(np.asarray(b, dtype=np.float64), (self.N, 3)), 3 * self.N)
+        """b: nodal velocity (N, 3), or one 3-vector for a constant field; c: a constant
+        reaction or nodal values (N,); f: nodal source (N,) or None."""
+        ba = np.asarray(b, dtype=np.float64)
+        bn, bc = (None, _f64(ba, 3)) if ba.shape == (3,) else \
+            (_f64(np.broadcast_to(ba, (self.N, 3)), 3 * self.N), None)
+        ca = np.asarray(c, dtype=np.float64)
+        cn, cc = (None, float(ca)) if ca.ndim == 0 else (_f64(np.broadcast_to(ca, (self.N,)), self.N), 0.0)
         fa = None if f is None else _f64(np.broadcast_to(np.asarray(f, dtype=np.float64), (self.N,)), self.N)
-        _check(_lib.afc_set_coefficients(self.h, float(eps), _dp(b), float(c), None if fa is None else _dp(fa)),
-               "afc_set_coefficients")
+        _check(_lib.afc_set_coefficients(self.h, float(eps), None if bn is None else _dp(bn),
+                                         None if bc is None else _dp(bc), None if cn is None else _dp(cn), cc,
+                                         None if fa is None else _dp(fa)), "afc_set_coefficients")
 
     def set_dirichlet(self, mask, values):
         m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))

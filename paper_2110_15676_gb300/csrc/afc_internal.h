@@ -118,6 +118,8 @@ struct afc_problem_s {
   bool coef_set = false;
   double eps = 0.0, c = 0.0;
   afc::DBuf<double> bnod, fnod;
+  afc::DBuf<double> cnod;                         // N: nodal reaction (when c_nodal)
+  bool c_nodal = false;
   afc::DBuf<uint8_t> dir;
   afc::DBuf<double> udir;
 
@@ -126,6 +128,8 @@ struct afc_problem_s {
   int family = 0, precision = 0;
   afc::DBuf<double> Mfull, Sfull, Kfull, Afull;   // K * N each
   afc::DBuf<double> AA;                           // K * N, low-order operator
+  afc::DBuf<double> Rfull;                        // K * N, (c_h phi_j, phi_i) for a nodal reaction
+  afc::DBuf<double> rl;                           // N: lumped reaction (c m_i or row sums of Rfull)
   afc::DBuf<double> m_up, d_up;                   // Kup * N, symmetric edge data
   afc::DBuf<double> kij_up, kji_up;               // Kup * N, MC: convective k_ij and k_ji of each pair i < j
   afc::DBuf<double> d2_up;                        // Kup * N, MC: 2 |d_ij|

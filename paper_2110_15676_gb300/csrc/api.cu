@@ -111,7 +111,7 @@ void destroy_all(afc_problem_s* p) {
                         &p->u, &p->u0, &p->ustage, &p->udot, &p->ut, &p->Rp, &p->Rm, &p->Fs, &p->Qp, &p->Qm,
                         &p->b0, &p->res, &p->delta, &p->umax, &p->umin, &p->tmp, &p->cn_a, &p->cn_s,
                         &p->scal, &p->part, &p->r_up, &p->mdt_up, &p->mLdt, &p->kij_up, &p->kji_up,
-                        &p->AG, &p->bA, &p->bB, &p->d2_up, &p->Fold};
+                        &p->AG, &p->bA, &p->bB, &p->d2_up, &p->Fold, &p->cnod, &p->Rfull, &p->rl};
   for (auto* b : dv) b->free_();
   p->Bst32.free_(); p->dinv_st32.free_(); p->Bcn32.free_(); p->dinv_cn32.free_();
   p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_(); p->clip.free_();
@@ -265,15 +265,35 @@ int afc_destroy(afc_problem p) {
   return AFC_OK;
 }
 
-int afc_set_coefficients(afc_problem p, double eps, const double* b_nodal, double c, const double* f_nodal) {
+int afc_set_coefficients(afc_problem p, double eps, const double* b_nodal, const double b_const[3],
+                         const double* c_nodal, double c_const, const double* f_nodal) {
   int st = check(p, false);
   if (st) return st;
-  if (!b_nodal || !(eps >= 0.0) || !(c >= 0.0) || !std::isfinite(eps) || !std::isfinite(c)) {
-    set_error("need b_nodal, eps >= 0 and c >= 0");
+  if ((!b_nodal && !b_const) || !(eps >= 0.0) || !std::isfinite(eps) ||
+      (!c_nodal && (!(c_const >= 0.0) || !std::isfinite(c_const)))) {
+    set_error("need b_nodal or b_const, eps >= 0 and c_const >= 0 (or c_nodal)");
     return AFC_E_INVALID;
   }
+  if (c_nodal)
+    for (int64_t i = 0; i < p->N; ++i)
+      if (!(c_nodal[i] >= 0.0) || !std::isfinite(c_nodal[i])) {
+        set_error("c_nodal must be finite and >= 0 at every node");
+        return AFC_E_INVALID;
+      }
+  std::vector<double> bc;
+  if (!b_nodal) {   // a constant velocity at every node
+    bc.resize(3 * p->N);
+    for (int64_t i = 0; i < p->N; ++i)
+      for (int d = 0; d < 3; ++d) bc[3 * i + d] = b_const[d];
+    b_nodal = bc.data();
+  }
   p->eps = eps;
-  p->c = c;
+  p->c = c_nodal ? 0.0 : c_const;
+  p->c_nodal = c_nodal != nullptr;
+  if (c_nodal) {
+    if ((st = p->cnod.alloc(p->N))) return st;
+    if ((st = to_device(p, p->cnod.p, c_nodal, p->N))) return st;
+  }
   if ((st = to_device(p, p->bnod.p, b_nodal, 3 * p->N))) return st;
   if (f_nodal) {
     if ((st = to_device(p, p->fnod.p, f_nodal, p->N))) return st;

@@ -65,6 +65,57 @@ __device__ void p1_row(const double X[4][3], const double B[4][3], int a, double
   }
 }
 
+// Row `a` of the reaction matrix (c_h phi_b, phi_a) of a tetrahedron for the linear
+// interpolant c_h of the nodal reaction Cn: int l_a l_b l_k = V (1 + d_ab + d_ak + d_bk
+// + 2 d_abk) / 120 (the integral of a product of barycentric coordinates).
+__device__ void p1_row_reaction(const double X[4][3], const double Cn[4], int a, double* R) {
+  double J[3][3], Ji[3][3], det;
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) J[r][q] = X[q + 1][r] - X[0][r];
+  inv3(J, Ji, det);
+  const double V = fabs(det) / 6.0;
+  for (int b = 0; b < 4; ++b) {
+    double s = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      const double t = 1.0 + (a == b) + (a == k) + (b == k) + 2.0 * (a == b && b == k);
+      s += t * Cn[k];
+    }
+    R[b] = V * s / 120.0;
+  }
+}
+
+// Row `a` of the trilinear reaction matrix, 2x2x2 Gauss points (exact on
+// parallelepipeds: degree 3 per reference coordinate).
+__device__ void q1_row_reaction(const double X[8][3], const double Cn[8], int a, double* R) {
+  const double g0 = 0.5 - 0.5 / sqrt(3.0), g1 = 0.5 + 0.5 / sqrt(3.0);
+  for (int b = 0; b < 8; ++b) R[b] = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    const double xi[3] = {(q & 4) ? g1 : g0, (q & 2) ? g1 : g0, (q & 1) ? g1 : g0};
+    double phi[8], dr[8][3];
+    for (int k = 0; k < 8; ++k) {
+      double f[3], df[3];
+      for (int d = 0; d < 3; ++d) {
+        bool bit = (k >> d) & 1;
+        f[d] = bit ? xi[d] : 1.0 - xi[d];
+        df[d] = bit ? 1.0 : -1.0;
+      }
+      phi[k] = f[0] * f[1] * f[2];
+      dr[k][0] = df[0] * f[1] * f[2];
+      dr[k][1] = f[0] * df[1] * f[2];
+      dr[k][2] = f[0] * f[1] * df[2];
+    }
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Ji[3][3], det;
+    for (int k = 0; k < 8; ++k)
+      for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) J[r][d] += X[k][r] * dr[k][d];
+    inv3(J, Ji, det);
+    double cq = 0.0;
+    for (int k = 0; k < 8; ++k) cq += phi[k] * Cn[k];
+    const double wd = 0.125 * fabs(det) * cq;
+    for (int b = 0; b < 8; ++b) R[b] += wd * phi[a] * phi[b];
+  }
+}
+
 // Row `a` of the trilinear element matrices, 2x2x2 Gauss points on [0,1]^3.
 __device__ void q1_row(const double X[8][3], const double B[8][3], int a, double* M, double* S, double* C) {
   const double g0 = 0.5 - 0.5 / sqrt(3.0), g1 = 0.5 + 0.5 / sqrt(3.0);
@@ -107,11 +158,11 @@ template <int NL>
 __global__ void k_assemble_rows(int64_t N, Offsets of, const double* __restrict__ xyz, const double* __restrict__ bn,
                                 const int32_t* __restrict__ conn, const int32_t* __restrict__ inc_ptr,
                                 const int32_t* __restrict__ inc, double* __restrict__ Mf, double* __restrict__ Sf,
-                                double* __restrict__ Kf) {
+                                double* __restrict__ Kf, const double* __restrict__ cn, double* __restrict__ Rf) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double am[kMaxOffsets], as[kMaxOffsets], ak[kMaxOffsets];
-  for (int k = 0; k < of.K; ++k) am[k] = as[k] = ak[k] = 0.0;
+  double am[kMaxOffsets], as[kMaxOffsets], ak[kMaxOffsets], ar[kMaxOffsets];
+  for (int k = 0; k < of.K; ++k) am[k] = as[k] = ak[k] = ar[k] = 0.0;
   for (int t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) {
     const int code = inc[t];
     const int64_t e = code >> 3;
@@ -125,37 +176,50 @@ __global__ void k_assemble_rows(int64_t N, Offsets of, const double* __restrict_
         B[k][d] = bn[3 * (int64_t)v[k] + d];
       }
     }
-    double M[NL], S[NL], C[NL];
+    double M[NL], S[NL], C[NL], R[NL];
     if (NL == 4) p1_row((const double(*)[3])X, (const double(*)[3])B, a, M, S, C);
     else q1_row((const double(*)[3])X, (const double(*)[3])B, a, M, S, C);
+    if (cn) {   // nodal reaction: its Galerkin matrix
+      double Cn[NL];
+      for (int k = 0; k < NL; ++k) Cn[k] = cn[v[k]];
+      if (NL == 4) p1_row_reaction((const double(*)[3])X, Cn, a, R);
+      else q1_row_reaction((const double(*)[3])X, Cn, a, R);
+    }
     for (int b = 0; b < NL; ++b) {
       int k = find_offset(of, v[b] - (int)i);
       am[k] += M[b];
       as[k] += S[b];
       ak[k] += C[b];
+      if (cn) ar[k] += R[b];
     }
   }
   for (int k = 0; k < of.K; ++k) {
     Mf[k * N + i] = am[k];
     Sf[k * N + i] = as[k];
     Kf[k * N + i] = ak[k];
+    if (cn) Rf[k * N + i] = ar[k];
   }
 }
 
-// mL, f = M_L f_nodal, and the matrix whose off-diagonals define D.
+// mL, f = M_L f_nodal, the lumped reaction rl (c m_i, or the row sums of the nodal
+// reaction's matrix Rf), and the matrix whose off-diagonals define D.
 __global__ void k_lumped_and_A(int64_t N, Offsets of, int family, double eps, double c, const double* __restrict__ Mf,
                                const double* __restrict__ Sf, const double* __restrict__ Kf,
-                               const double* __restrict__ fn, double* __restrict__ mL, double* __restrict__ f,
+                               const double* __restrict__ Rf, const double* __restrict__ fn,
+                               double* __restrict__ mL, double* __restrict__ f, double* __restrict__ rl,
                                double* __restrict__ Af) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double s = 0.0;
+  double s = 0.0, sr = 0.0;
   for (int k = 0; k < of.K; ++k) s += Mf[k * N + i];
+  if (Rf)
+    for (int k = 0; k < of.K; ++k) sr += Rf[k * N + i];
   mL[i] = s;
   f[i] = s * fn[i];
+  rl[i] = Rf ? sr : c * s;
   for (int k = 0; k < of.K; ++k) {
     size_t q = k * N + i;
-    Af[q] = family == AFC_FAMILY_FCT ? (eps * Sf[q] + Kf[q]) + c * Mf[q] : Kf[q];
+    Af[q] = family == AFC_FAMILY_FCT ? (eps * Sf[q] + Kf[q]) + (Rf ? Rf[q] : c * Mf[q]) : Kf[q];
   }
 }
 
@@ -178,10 +242,10 @@ __global__ void k_upwind_edges(int64_t N, Offsets of, const unsigned long long* 
   }
 }
 
-// AA = A + D (FCT) or K + D + eps S + c M_L (MC), full rows.
-__global__ void k_low_order(int64_t N, Offsets of, int family, double eps, double c,
+// AA = A + D (FCT) or K + D + eps S + (lumped reaction) (MC), full rows.
+__global__ void k_low_order(int64_t N, Offsets of, int family, double eps, const double* __restrict__ rl,
                             const unsigned long long* __restrict__ mask, const double* __restrict__ Af,
-                            const double* __restrict__ Sf, const double* __restrict__ mL,
+                            const double* __restrict__ Sf,
                             const double* __restrict__ dup, double* __restrict__ AAf) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -200,15 +264,15 @@ __global__ void k_low_order(int64_t N, Offsets of, int family, double eps, doubl
     AAf[k * N + i] = v;
   }
   double dv = Af[of.Kup * N + i] + (-dsum);
-  if (family == AFC_FAMILY_MC) dv = (dv + eps * Sf[of.Kup * N + i]) + c * mL[i];
+  if (family == AFC_FAMILY_MC) dv = (dv + eps * Sf[of.Kup * N + i]) + rl[i];
   AAf[of.Kup * N + i] = dv;
 }
 
 // MC family: the convective entries of each pair i < j at row i (k_ij, k_ji) and the
 // unlimited operator AG = K + eps S + c M_L (AA without D) of the residual.
-__global__ void k_mc_extras(int64_t N, Offsets of, double eps, double c, const unsigned long long* __restrict__ mask,
-                            const double* __restrict__ Kf, const double* __restrict__ Sf,
-                            const double* __restrict__ mL, const double* __restrict__ dup,
+__global__ void k_mc_extras(int64_t N, Offsets of, double eps, const double* __restrict__ rl,
+                            const unsigned long long* __restrict__ mask,
+                            const double* __restrict__ Kf, const double* __restrict__ Sf, const double* __restrict__ dup,
                             double* __restrict__ kij, double* __restrict__ kji, double* __restrict__ d2,
                             float* __restrict__ pairf, double* __restrict__ AG) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -227,7 +291,7 @@ __global__ void k_mc_extras(int64_t N, Offsets of, double eps, double c, const u
   }
   for (int k = 0; k < of.K; ++k) {
     double v = Kf[k * N + i] + eps * Sf[k * N + i];
-    if (k == of.Kup) v = v + c * mL[i];
+    if (k == of.Kup) v = v + rl[i];
     AG[k * N + i] = v;
   }
 }
@@ -264,28 +328,33 @@ int assemble_device(afc_problem_s* p, int family, int precision) {
   if ((st = p->Mfull.alloc(K * N)) || (st = p->Sfull.alloc(K * N)) || (st = p->Kfull.alloc(K * N)) ||
       (st = p->Afull.alloc(K * N)) || (st = p->AA.alloc(K * N)) || (st = p->m_up.alloc(Kup * N)) ||
       (st = p->d_up.alloc(Kup * N)) || (st = p->mL.alloc(N, p->pad)) || (st = p->f.alloc(N, p->pad)) ||
-      (st = p->Bst.alloc(K * N)) || (st = p->dinv_st.alloc(N, p->pad)) || (st = p->r_up.alloc(Kup * N)))
+      (st = p->Bst.alloc(K * N)) || (st = p->dinv_st.alloc(N, p->pad)) || (st = p->r_up.alloc(Kup * N)) ||
+      (st = p->rl.alloc(N, p->pad)))
     return st;
+  const bool nodal_c = p->c_nodal;
+  if (nodal_c && (st = p->Rfull.alloc(K * N))) return st;
+  const double* cn = nodal_c ? p->cnod.p : nullptr;
+  double* Rf = nodal_c ? p->Rfull.p : nullptr;
   const int64_t g = grid_for(N);
   if (p->mesh.nl == 4)
     AFC_LAUNCH(p, "k_assemble_rows", k_assemble_rows<4><<<g, kBlock, 0, s>>>(N, p->offs, p->xyz.p, p->bnod.p, p->conn.p, p->inc_ptr.p, p->inc.p,
-                                             p->Mfull.p, p->Sfull.p, p->Kfull.p));
+                                             p->Mfull.p, p->Sfull.p, p->Kfull.p, cn, Rf));
   else
     AFC_LAUNCH(p, "k_assemble_rows", k_assemble_rows<8><<<grid_for(N, 128), 128, 0, s>>>(N, p->offs, p->xyz.p, p->bnod.p, p->conn.p, p->inc_ptr.p,
-                                                         p->inc.p, p->Mfull.p, p->Sfull.p, p->Kfull.p));
+                                                         p->inc.p, p->Mfull.p, p->Sfull.p, p->Kfull.p, cn, Rf));
   AFC_CUDA(cudaGetLastError());
-  AFC_LAUNCH(p, "k_lumped_and_A", k_lumped_and_A<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->Mfull.p, p->Sfull.p, p->Kfull.p, p->fnod.p,
-                                      p->mL.p, p->f.p, p->Afull.p));
+  AFC_LAUNCH(p, "k_lumped_and_A", k_lumped_and_A<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->Mfull.p, p->Sfull.p, p->Kfull.p, Rf,
+                                      p->fnod.p, p->mL.p, p->f.p, p->rl.p, p->Afull.p));
   AFC_LAUNCH(p, "k_upwind_edges", k_upwind_edges<<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->Afull.p, p->d_up.p));
-  AFC_LAUNCH(p, "k_low_order", k_low_order<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->c, p->mask.p, p->Afull.p, p->Sfull.p, p->mL.p,
+  AFC_LAUNCH(p, "k_low_order", k_low_order<<<g, kBlock, 0, s>>>(N, p->offs, family, p->eps, p->rl.p, p->mask.p, p->Afull.p, p->Sfull.p,
                                    p->d_up.p, p->AA.p));
   if (family == AFC_FAMILY_MC) {
     if ((st = p->kij_up.alloc(Kup * N)) || (st = p->kji_up.alloc(Kup * N)) || (st = p->d2_up.alloc(Kup * N)) ||
         (st = p->AG.alloc(K * N)) || (st = p->clip.alloc(N, p->pad)) || (st = p->pairf.alloc(3 * Kup * N)) ||
         (st = p->nodef.alloc(N, p->pad)))
       return st;
-    AFC_LAUNCH(p, "k_mc_extras", k_mc_extras<<<g, kBlock, 0, s>>>(N, p->offs, p->eps, p->c, p->mask.p, p->Kfull.p,
-                                                                   p->Sfull.p, p->mL.p, p->d_up.p, p->kij_up.p,
+    AFC_LAUNCH(p, "k_mc_extras", k_mc_extras<<<g, kBlock, 0, s>>>(N, p->offs, p->eps, p->rl.p, p->mask.p, p->Kfull.p,
+                                                                   p->Sfull.p, p->d_up.p, p->kij_up.p,
                                                                    p->kji_up.p, p->d2_up.p, p->pairf.p, p->AG.p));
     if (precision == AFC_MIXED && (st = mc_pair_setup(p))) return st;
   }

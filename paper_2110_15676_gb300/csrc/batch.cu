@@ -503,13 +503,16 @@ int batch_minmax(afc_batch_s* b) {
 }
 
 // The instances' input ranges for afc_stats.dmp_violation: measured once for all when
-// any instance's range is not known from an earlier call.
-int batch_input_ranges(afc_batch_s* b) {
+// any instance's range is not known from an earlier call.  k_batch_minmax reads the
+// instance table, so the table of this call's launch shape is built first (the
+// device table is uninitialised until the first build).
+int batch_input_ranges(afc_batch_s* b, int block, const double* dt, const afc_opts* o) {
   bool all = true;
   for (auto* p : b->list) all = all && p->u_range_valid;
   if (all) return AFC_OK;
-  int st = batch_minmax(b);
+  int st = build_table(b, block, dt, o->dt, o->precision == AFC_MIXED);
   if (st) return st;
+  if ((st = batch_minmax(b))) return st;
   AFC_CUDA(cudaStreamSynchronize(b->stream));
   for (size_t q = 0; q < b->list.size(); ++q) {
     b->list[q]->u_lo = b->mm_h[2 * q];
@@ -646,7 +649,7 @@ extern "C" int afc_batch_step(afc_batch b, const afc_opts* o, const double* dt, 
   if (nsteps < 0) { set_error("nsteps must be >= 0"); return AFC_E_INVALID; }
   if (cudaSetDevice(b->device) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
   const afc_batch_tuning t = effective_tuning(b, o);
-  if ((st = batch_input_ranges(b))) return st;
+  if ((st = batch_input_ranges(b, t.block, dt, o))) return st;
   if ((st = run_steps(b, o, dt, nsteps, t))) return st;
   return batch_status(b, stats, nsteps * (o->scheme == AFC_SSP2 ? 2 : 3));
 }

@@ -259,9 +259,7 @@ __global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, 
       float h, l;
       two_sum(sh, sl, h, l);
       rv = widen_exact(h) + widen_exact(l);
-      // res^2 for the stopping test, from the high part on the FP32 pipe (relative
-      // error ~2^-23, far inside what the test ||res|| < sqrt(N) tol needs)
-      r2 = widen_exact(__fmul_rn(h, h));
+      r2 = rv * rv;
     }
     res[i] = rv;
   }

@@ -167,7 +167,8 @@ int build_problem(afc_server_s* s, Request& r) {
   const afc_request& q = r.spec;
   int st;
   if ((st = afc_create_structured(q.elem, q.n[0], q.n[1], q.n[2], q.lo, q.hi, s->device, r.stream, &r.p))) return st;
-  if ((st = afc_set_coefficients(r.p, q.eps, r.b.data(), q.c, r.f.empty() ? nullptr : r.f.data()))) return st;
+  if ((st = afc_set_coefficients(r.p, q.eps, r.b.data(), nullptr, nullptr, q.c, r.f.empty() ? nullptr : r.f.data())))
+    return st;
   if ((st = afc_set_dirichlet(r.p, r.mask.data(), r.u_dir.data()))) return st;
   if ((st = afc_assemble(r.p, q.family, q.opts.precision))) return st;
   if ((st = afc_set_solution(r.p, r.u0.data(), 0))) return st;

@@ -55,6 +55,35 @@ def test_assembly_matches_oracle(afc, elem, family, n, lo, hi):
     assert info["nnz"] == o.MC.nnz and info["n_nodes"] == o.mesh.n_nodes
 
 
+@pytest.mark.parametrize("elem", ["p1", "q1"])
+@pytest.mark.parametrize("family", ["fct", "mc"])
+def test_nodal_reaction_and_constant_velocity_assembly(afc, elem, family):
+    """afc_set_coefficients with a nodal reaction (the Galerkin matrix (c_h phi_j,
+    phi_i); lumped in the MC family) and a constant velocity b_const: every matrix
+    against the oracle's assembly of the same coefficients."""
+    n, lo, hi = (7, 6, 5), (0, -1, 0.5), (2, 0.5, 1.25)
+    wl = random_workload(elem, n, seed=31, lo=lo, hi=hi)
+    rng = np.random.default_rng(32)
+    c_nodal = rng.uniform(0.0, 2.0, wl.n_nodes)
+    b_const = np.array([0.3, -0.7, 0.45])
+    o = oracle_problem(wl.elem, wl.n, b_const, wl.eps, c_nodal, wl.f, wl.dir_mask, wl.u_dir, family, wl.lo, wl.hi)
+    g = gpu_problem(wl.elem, wl.n, b_const, wl.eps, c_nodal, wl.f, wl.dir_mask, wl.u_dir, family, "fp64",
+                    wl.lo, wl.hi)
+    for which, M in _matrices(o).items():
+        G = csr_of(g, which)
+        scale = max(np.abs(M.data).max(), 1e-300)
+        diff = (G - M).tocsr()
+        assert (np.abs(diff.data).max() if diff.nnz else 0.0) <= PASS_TOL * scale * 10, which
+    if family == "mc":   # the stationary solve uses the lumped nodal reaction in AA and in its residual
+        u_ref, _ = O.mc_stationary(o, tol=1e-12, omega=0.5, ksp="direct", max_outer=2000)
+        g.set_solution(wl.u0)
+        st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, fp_tol=1e-12, omega=0.5,
+                                                 ksp=afc.AFC_KSP_GMRES, ksp_atol=1e-14, fp_maxit=2000))
+        assert st["status"] == afc.AFC_OK
+        assert relerr(g.get_solution(), u_ref) < STEP_TOL
+    g.close()
+
+
 def _element_meshes():
     # two tetrahedra sharing a face
     two = (np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1.0]]), np.array([[0, 1, 2, 3], [1, 2, 3, 4]]))

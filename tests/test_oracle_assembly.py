@@ -150,3 +150,30 @@ def test_upwinding_and_m_matrix(elem, fam):
     assert (np.diag(AA) > 0).all()
     # row sums of AA: c m_i (consistent reaction in FCT, lumped in MC: both sum to c m_i)
     assert np.abs(AA.sum(axis=1) - c * prob.mL).max() < 1e-13 * np.abs(AA).max()
+
+
+@pytest.mark.parametrize("elem", ["p1", "q1"])
+def test_nodal_reaction_matrix_closed_forms(elem):
+    """The Galerkin reaction term (c_h phi_j, phi_i) with c interpolated from nodal values:
+    a constant c gives c M_C, and for c = x, v = y, w = z (all in the FE space)
+    1^T R 1 = int x = 1/2 and v^T R w = int x y z = 1/8; the MC system lumps R to its
+    row sums (reading A9), so its row sums of AA are int c phi_i."""
+    n = 5
+    xyz = W.grid_coords(n)
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    mesh = O.structured_mesh(elem, n)
+    N = len(xyz)
+    b = np.zeros((N, 3))
+    dm = np.zeros(N, bool)
+    p_const = O.assemble(mesh, 0.0, b, 0.7, np.zeros(N), dm, np.zeros(N))
+    p_nodal = O.assemble(mesh, 0.0, b, np.full(N, 0.7), np.zeros(N), dm, np.zeros(N))
+    assert abs(p_nodal.A - p_const.A).max() <= 1e-15 * abs(p_const.A).max()
+    p_x = O.assemble(mesh, 0.0, b, x, np.zeros(N), dm, np.zeros(N))
+    R = p_x.A                                  # eps = 0, b = 0: A = R
+    one = np.ones(N)
+    assert abs(one @ (R @ one) - 0.5) < 1e-14
+    assert abs(y @ (R @ z) - 0.125) < 1e-14
+    m_x = O.assemble(mesh, 0.0, b, x, np.zeros(N), dm, np.zeros(N), "mc")
+    rs = np.asarray(m_x.AA.sum(axis=1)).ravel()   # K = D = S-part = 0: AA = diag(row sums of R)
+    assert np.abs(rs - np.asarray(R.sum(axis=1)).ravel()).max() < 1e-16
+    assert abs(rs.sum() - 0.5) < 1e-14
