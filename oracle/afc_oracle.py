@@ -328,10 +328,11 @@ def zalesak_limiter(prob: Problem, r, u_tilde, dt, mode="zalesak"):
     Qp = np.zeros(N); Qm = np.zeros(N)
     np.maximum.at(Qp, I, u_tilde[J] - u_tilde[I])
     np.minimum.at(Qm, I, u_tilde[J] - u_tilde[I])
-    # step 3
+    # step 3: m_i Q_i / (dt P_i), taken as (m_i Q_i / dt) / P_i so that a subnormal
+    # P_i != 0, whose product with dt underflows to 0, cannot make it 0 / 0
     with np.errstate(divide="ignore", invalid="ignore"):
-        Rp = np.where(Pp != 0.0, np.minimum(1.0, prob.mL * Qp / (dt * Pp)), 1.0)
-        Rm = np.where(Pm != 0.0, np.minimum(1.0, prob.mL * Qm / (dt * Pm)), 1.0)
+        Rp = np.where(Pp != 0.0, np.minimum(1.0, (prob.mL * Qp / dt) / Pp), 1.0)
+        Rm = np.where(Pm != 0.0, np.minimum(1.0, (prob.mL * Qm / dt) / Pm), 1.0)
     Rp[prob.dir_mask] = 1.0
     Rm[prob.dir_mask] = 1.0
     # step 4

@@ -16,10 +16,11 @@
 //  1. k_mcp_split:   u -> pairs (integer pipe);
 //  2. k_mcp_rows:    per row, y = f - AG u and the bounds u_max, u_min over N_i in
 //                    one pass over the row's neighbours (the same state loads serve
-//                    both), A = u_max - u, B = u - u_min; clears the clip mask;
+//                    both), A = u_max - u, B = u - u_min;
 //  3. k_mcp_edges:   per pair i < j, the exact single-precision pre-test of mc.cu on
 //                    the high parts, and for the pairs it cannot clear, T_i, T_j and
-//                    c_ij in pair arithmetic (stored at row i, bit ku of row i's mask);
+//                    c_ij in pair arithmetic (stored at row i), and every row's clip
+//                    mask (bit ku for a clipped pair);
 //  4. k_mcp_residual: res = y - sum_j c_ij on free rows (0 on Dirichlet rows), in
 //                    pairs, rounded to double once; block partials of res^2.
 // Accuracy: every value carries a relative error of at most 2^-48 and every product
@@ -43,8 +44,7 @@ template <int KT>
 __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
                                                      const float2* __restrict__ up, const float2* __restrict__ AGp,
                                                      const float2* __restrict__ fp, float2* __restrict__ yp,
-                                                     float2* __restrict__ abh, float2* __restrict__ abl,
-                                                     unsigned int* __restrict__ clip) {
+                                                     float2* __restrict__ abh, float2* __restrict__ abl) {
   const int K = KT > 0 ? KT : of.K;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -93,7 +93,6 @@ __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, cons
   if (Bh < 0.f) Bh = Bl = 0.f;
   abh[i] = make_float2(Ah, Bh);
   abl[i] = make_float2(Al, Bl);
-  clip[i] = 0u;
 }
 
 // The pre-test of mc.cu (k_mc_edges), on the high parts: T = 2|d| X - a |D| is
@@ -121,34 +120,37 @@ __device__ __forceinline__ void side_value(float d2h, float d2l, float xh, float
   two_sum(s, e, th, tl);
 }
 
-// One pair (i, j = i + o) of row i given its loaded data; returns true and the clipped
-// amount c_ij (c = -min(0, T_i, T_j) for r_ij > 0, min(0, T_i, T_j) for r_ij < 0) when
-// the pair is clipped.  The low parts of 2|d|, a_ij, a_ji are loaded only here, for the
-// pairs the pre-test cannot clear.
-__device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __restrict__ pfl,
-                                          const float2* __restrict__ abl, int64_t i, int64_t j, float d2h, float aih,
-                                          float ajh, float2 ui, float2 uj, float2 bi, float2 bj, float2& c) {
-  const bool side_i = aih > 0.f, side_j = ajh > 0.f;
-  if (!(d2h > 0.f) || !(side_i || side_j)) return false;   // d = 0, or no side can clip
-  if (ui.x == uj.x && ui.y == uj.y) return false;           // u_i = u_j: r = 0
-  const bool rpos = pair_gt(ui.x, ui.y, uj.x, uj.y);        // r_ij = d (u_j - u_i) > 0  <=>  u_j < u_i
+// Everything one pair slot (i, j = i + o) needs, loaded at once.  On the states the
+// fixed point produces nearly every warp has a pair the pre-test cannot clear, so the
+// low parts are read in the same round trip instead of a dependent second one.
+struct PairLoad {
+  float d2h, aih, ajh, d2l, ail, ajl;   // 2|d|, a_ij, a_ji: high and low parts
+  float2 ui, uj;                        // the states
+  float2 bhi, bhj, bli, blj;            // (A, B) high and low parts at i and j
+};
+
+// The clipped amount c_ij (c = -min(0, T_i, T_j) for r_ij > 0, min(0, T_i, T_j) for
+// r_ij < 0); returns false when the pair is not clipped.
+__device__ __forceinline__ bool pair_clip(const PairLoad& L, float2& c) {
+  const bool side_i = L.aih > 0.f, side_j = L.ajh > 0.f;
+  if (!(L.d2h > 0.f) || !(side_i || side_j)) return false;       // d = 0, or no side can clip
+  if (L.ui.x == L.uj.x && L.ui.y == L.uj.y) return false;         // u_i = u_j: r = 0
+  const bool rpos = pair_gt(L.ui.x, L.ui.y, L.uj.x, L.uj.y);      // r_ij = d (u_j - u_i) > 0  <=>  u_j < u_i
   // room of each side: r > 0 uses A_i = u_i^max - u_i and B_j; r < 0 uses B_i and A_j
-  const float xih = rpos ? bi.x : bi.y, xjh = rpos ? bj.y : bj.x;
-  if (ui.x != uj.x) {
-    const bool ok_i = !side_i || side_clear(d2h, aih, xih, ui.x, uj.x);
-    const bool ok_j = !side_j || side_clear(d2h, ajh, xjh, ui.x, uj.x);
+  const float xih = rpos ? L.bhi.x : L.bhi.y, xjh = rpos ? L.bhj.y : L.bhj.x;
+  if (L.ui.x != L.uj.x) {
+    const bool ok_i = !side_i || side_clear(L.d2h, L.aih, xih, L.ui.x, L.uj.x);
+    const bool ok_j = !side_j || side_clear(L.d2h, L.ajh, xjh, L.ui.x, L.uj.x);
     if (ok_i && ok_j) return false;
   }
-  const float d2l = __ldcs(pfl + q), ail = __ldcs(pfl + KN + q), ajl = __ldcs(pfl + 2 * KN + q);
-  const float2 li = abl[i], lj = abl[j];
-  const float xil = rpos ? li.x : li.y, xjl = rpos ? lj.y : lj.x;
+  const float xil = rpos ? L.bli.x : L.bli.y, xjl = rpos ? L.blj.y : L.blj.x;
   float Dh, Dl;   // |u_j - u_i|
-  if (rpos) pair_sub(ui.x, ui.y, uj.x, uj.y, Dh, Dl);
-  else pair_sub(uj.x, uj.y, ui.x, ui.y, Dh, Dl);
+  if (rpos) pair_sub(L.ui.x, L.ui.y, L.uj.x, L.uj.y, Dh, Dl);
+  else pair_sub(L.uj.x, L.uj.y, L.ui.x, L.ui.y, Dh, Dl);
   float mh = 0.f, ml = 0.f;   // min(0, T_i, T_j)
   if (side_i) {
     float th, tl;
-    side_value(d2h, d2l, xih, xil, aih, ail, Dh, Dl, th, tl);
+    side_value(L.d2h, L.d2l, xih, xil, L.aih, L.ail, Dh, Dl, th, tl);
     if (pair_gt(mh, ml, th, tl)) {
       mh = th;
       ml = tl;
@@ -156,7 +158,7 @@ __device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __
   }
   if (side_j) {
     float th, tl;
-    side_value(d2h, d2l, xjh, xjl, ajh, ajl, Dh, Dl, th, tl);
+    side_value(L.d2h, L.d2l, xjh, xjl, L.ajh, L.ajl, Dh, Dl, th, tl);
     if (pair_gt(mh, ml, th, tl)) {
       mh = th;
       ml = tl;
@@ -167,11 +169,12 @@ __device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __
   return true;
 }
 
-// Clipped amount c_ij of every pair i < j (stored at row i, only where nonzero; the
-// row's clip mask gets bit ku), one thread per pair slot (ku, i): a block covers 32
-// consecutive rows (threadIdx.x) and all upper offsets (threadIdx.y).  Every load a
-// pair needs for its pre-test is issued at once (one round trip to memory); only the
-// pairs the pre-test cannot clear load the low parts.
+// Clipped amount c_ij of every pair i < j (stored at row i, only where nonzero) and
+// every row's clip mask (bit ku: the pair with upper offset ku is clipped), one thread
+// per pair slot (ku, i): a block covers 32 consecutive rows (threadIdx.x) and all
+// upper offsets (threadIdx.y).  The 2|d|, k_ij, k_ji data are read once per sweep and
+// streamed past L2, so that the node arrays (gathered at i and at i + o) stay there;
+// the masks meet in shared memory and are stored whole, one word per row.
 template <int KT>
 __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf, const float* __restrict__ pfl,
                             const float2* __restrict__ up, const float2* __restrict__ abh,
@@ -180,19 +183,34 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf,
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   const int ku = threadIdx.y;
   const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
-  if (i >= N) return;
-  const int64_t q = (int64_t)ku * N + i;
-  const int64_t j = i + of.o[Kup + 1 + ku];
-  const int64_t KN = (int64_t)Kup * N;
-  // 2|d|, a_ij, a_ji (high parts), streamed past L2 so that the node arrays stay there
-  const float d2h = __ldcs(pf + q), aih = __ldcs(pf + KN + q), ajh = __ldcs(pf + 2 * KN + q);
-  const float2 ui = up[i], uj = up[j];
-  const float2 bi = abh[i], bj = abh[j];
-  float2 c;
-  if (pair_clip(q, KN, pfl, abl, i, j, d2h, aih, ajh, ui, uj, bi, bj, c)) {
-    c_up[q] = c;
-    atomicOr(clip + i, 1u << ku);
+  __shared__ unsigned int smask[32];
+  if (ku == 0) smask[threadIdx.x] = 0u;
+  __syncthreads();
+  if (i < N) {
+    const int64_t q = (int64_t)ku * N + i;
+    const int64_t j = i + of.o[Kup + 1 + ku];
+    const int64_t KN = (int64_t)Kup * N;
+    PairLoad L;
+    L.d2h = __ldcs(pf + q);
+    L.aih = __ldcs(pf + KN + q);
+    L.ajh = __ldcs(pf + 2 * KN + q);
+    L.d2l = __ldcs(pfl + q);
+    L.ail = __ldcs(pfl + KN + q);
+    L.ajl = __ldcs(pfl + 2 * KN + q);
+    L.ui = up[i];
+    L.uj = up[j];
+    L.bhi = abh[i];
+    L.bhj = abh[j];
+    L.bli = abl[i];
+    L.blj = abl[j];
+    float2 c;
+    if (pair_clip(L, c)) {
+      c_up[q] = c;
+      atomicOr(smask + threadIdx.x, 1u << ku);
+    }
   }
+  __syncthreads();
+  if (ku == 0 && i < N) clip[i] = smask[threadIdx.x];
 }
 
 template <int KT>
@@ -310,8 +328,7 @@ int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
     AFC_LAUNCH(p, "k_mcp_rows", k_mcp_rows<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->up2.p, p->AGp.p,
-                                                                     p->fp2.p, p->yp2.p, p->abh2.p, p->abl2.p,
-                                                                     p->clip.p));
+                                                                     p->fp2.p, p->yp2.p, p->abh2.p, p->abl2.p));
     if (limiter == AFC_LIM_MC)
       AFC_LAUNCH(p, "k_mcp_edges", k_mcp_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(
                                        N, p->offs, p->pairf.p, p->pairf_lo.p, p->up2.p, p->abh2.p, p->abl2.p,

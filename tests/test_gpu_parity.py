@@ -74,14 +74,23 @@ def test_nodal_reaction_and_constant_velocity_assembly(afc, elem, family):
         scale = max(np.abs(M.data).max(), 1e-300)
         diff = (G - M).tocsr()
         assert (np.abs(diff.data).max() if diff.nnz else 0.0) <= PASS_TOL * scale * 10, which
-    if family == "mc":   # the stationary solve uses the lumped nodal reaction in AA and in its residual
-        u_ref, _ = O.mc_stationary(o, tol=1e-12, omega=0.5, ksp="direct", max_outer=2000)
+    g.close()
+    if family == "mc":
+        # the stationary MC solve of the inflow problem with the nodal reaction 0.5 + x,
+        # which enters AA and the residual lumped
+        wl = W.stationary_inflow(elem, 9)
+        c_nodal = 0.5 + W.grid_coords(wl.n)[:, 0]
+        b_const = np.array([1.0, -0.5, 0.25])
+        o = oracle_problem(wl.elem, wl.n, b_const, wl.eps, c_nodal, wl.f, wl.dir_mask, wl.u_dir, "mc")
+        g = gpu_problem(wl.elem, wl.n, b_const, wl.eps, c_nodal, wl.f, wl.dir_mask, wl.u_dir, "mc")
+        u_ref, st_o = O.mc_stationary(o, tol=1e-12, omega=0.5, ksp="direct", max_outer=3000)
+        assert st_o["converged"]
         g.set_solution(wl.u0)
         st = g.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, fp_tol=1e-12, omega=0.5,
-                                                 ksp=afc.AFC_KSP_GMRES, ksp_atol=1e-14, fp_maxit=2000))
+                                                 ksp=afc.AFC_KSP_GMRES, ksp_atol=1e-14, fp_maxit=3000))
         assert st["status"] == afc.AFC_OK
         assert relerr(g.get_solution(), u_ref) < STEP_TOL
-    g.close()
+        g.close()
 
 
 def _element_meshes():
