@@ -207,7 +207,16 @@ def _roofline(name, kms, kcount, work_flops, share):
             "avg_launch_us": kms / kcount * 1e3, "share": share}
 
 
-def _mc_solve(afc, P, wl, torch, stream, rtol=1e-6, ref=None, sweep_ms=None):
+# Inner tolerance of the stationary MC solves (config 3 and the serving requests): the
+# relative GMRES reduction per fixed-point correction.  Measured on the config-3 solve
+# (bench.py --only-mc-sweep --mc-inner-rtols): every inner tolerance from 1e-6 to 1e-1
+# takes the same ~360 corrections and ends 1.27e-3 to 1.28e-3 from a reference
+# converged to 1e-13, so the outer stop decides the accuracy; 1e-2 needs 19 GMRES
+# iterations per correction instead of 182 at 1e-6.
+MC_INNER_RTOL = 1e-2
+
+
+def _mc_solve(afc, P, wl, torch, stream, rtol=MC_INNER_RTOL, ref=None, sweep_ms=None):
     # the whole stationary MC solve of this workload (damped fixed point, omega = 0.5,
     # tol 1e-10, mixed-precision Jacobi-GMRES(20) inner solves to a relative rtol);
     # with ref, also the largest difference from that solution relative to its maximum
@@ -234,7 +243,7 @@ def _mc_solve(afc, P, wl, torch, stream, rtol=1e-6, ref=None, sweep_ms=None):
            "options": f"omega 0.5, tol 1e-10, mixed: FP32 Jacobi-GMRES(20) rtol {rtol:g}, float-pair MC residual, "
                       f"FP64 outer"}
     if ref is not None:
-        out["rel_diff_vs_rtol_1e-6"] = float(np.abs(u_sol - ref).max() / np.abs(ref).max())
+        out["rel_diff_vs_main_solve"] = float(np.abs(u_sol - ref).max() / np.abs(ref).max())
     if sweep_ms is not None and sst["inner_its"] > 0:
         # the inner solves' share: the solve's time without its residual sweeps (one per
         # fixed-point iteration and a final one), per GMRES iteration, against the
@@ -268,7 +277,7 @@ def mc_sweep(afc, W, torch, flush, stream, reps, solve=True, inner_rtols=()):
     P.set_solution(wl.u0)
     # (host-driven loop: the same arithmetic as the graph, and its kernels stay visible to profilers)
     P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
-                                        ksp_rtol=1e-6, fp_fixed_its=6, precision=afc.AFC_MIXED, graph=0))
+                                        ksp_rtol=MC_INNER_RTOL, fp_fixed_its=6, precision=afc.AFC_MIXED, graph=0))
     info = P.info()
     N, nnz, E = info["n_nodes"], info["nnz"], info["n_edges"]
     for _ in range(3):
@@ -296,8 +305,23 @@ def mc_sweep(afc, W, torch, flush, stream, reps, solve=True, inner_rtols=()):
     if solve:
         solve_out, u_ref = _mc_solve(afc, P, wl, torch, stream, sweep_ms=ms / reps)
         if inner_rtols:
-            inner = {f"{r:g}": _mc_solve(afc, P, wl, torch, stream, rtol=r, ref=u_ref, sweep_ms=ms / reps)[0]
-                     for r in inner_rtols}
+            # a reference converged far below the stopping tolerance (FP64 throughout, inner
+            # GMRES to 1e-10 relative, fixed point to 1e-13): how far each solve to 1e-10 lies
+            # from the fixed point itself, for every inner tolerance
+            P.set_solution(wl.u0)
+            rst = P.solve_stationary(afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES,
+                                                      ksp_atol=0.0, ksp_rtol=1e-10, ksp_maxit=5000, fp_tol=1e-13,
+                                                      fp_maxit=3000, precision=afc.AFC_FP64))
+            u_star = P.get_solution()
+            scale = np.abs(u_star).max()
+            inner = {"reference": {"fixed_point_its": rst["outer_its"], "gmres_its": rst["inner_its"],
+                                   "status": rst["status"], "res_final": rst["res_final"],
+                                   "options": "FP64, inner GMRES(20) rtol 1e-10, fixed point tol 1e-13"},
+                     f"{MC_INNER_RTOL:g}": {"rel_err_vs_reference": float(np.abs(u_ref - u_star).max() / scale)}}
+            for r in inner_rtols:
+                o_r, u_r = _mc_solve(afc, P, wl, torch, stream, rtol=r, ref=u_ref, sweep_ms=ms / reps)
+                o_r["rel_err_vs_reference"] = float(np.abs(u_r - u_star).max() / scale)
+                inner[f"{r:g}"] = o_r
     # algorithmic work of one sweep (design notes): FP64 flops 14 per pair + 2 per entry;
     # bytes of the CSR count 4(N+1) + 12 nnz + 24 E + 24 N
     flops = 14.0 * E + 2.0 * nnz
@@ -427,7 +451,7 @@ def serving(afc, W, rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), count=48, see
         if kind == "transient":
             return afc.default_opts(scheme=afc.AFC_SSP3, precision=prec)
         return afc.default_opts(limiter=afc.AFC_LIM_MC, omega=0.5, ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0,
-                                ksp_rtol=1e-6, fp_tol=1e-8, fp_maxit=stat_maxit, precision=prec)
+                                ksp_rtol=MC_INNER_RTOL, fp_tol=1e-8, fp_maxit=stat_maxit, precision=prec)
 
     def reqs(prec):
         out = []
@@ -495,7 +519,8 @@ def serving(afc, W, rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), count=48, see
     n_st = sum(k == "stationary" for k, _ in mix)
     return {"workload": f"{count} requests per rate (numpy default_rng({seed})): {n_st} stationary MC (inflow problem, "
                         f"omega 0.5, tol 1e-8, at most {stat_maxit} fixed-point iterations, Jacobi-GMRES(20) rtol "
-                        f"1e-6), {count - n_st} transient SSP3 Zalesak (50 steps, CFL 0.5); P1/Q1, n in [17, 97], "
+                        f"{MC_INNER_RTOL:g}), {count - n_st} transient SSP3 Zalesak (50 steps, CFL 0.5); P1/Q1, "
+                        f"n in [17, 97], "
                         f"eps log-uniform [1e-8, 1e-4], c in [0, 1]; Poisson arrivals",
             "rates": rows, "mixed_max_rel_diff_vs_fp64": diff,
             "arms": "batched_mixed: 4 builders, continuous batching of transient requests, 8 concurrent stationary "

@@ -199,6 +199,16 @@ constexpr int S_BERR = 19;     // persistent BiCGStab: a grid barrier gave up wa
 static_assert(S_CYCLES > S_NO_REORTH && S_BERR > S_CYCLES && S_BERR < S_CS, "slot range");
 static_assert(S_BERR == kKrylovBarrierErrSlot, "slot number shared with graph.cu");
 
+// A solver flag (a double slot holding 0 or a positive code) tested on its bit pattern:
+// a compare of doubles issues on GB300's FP64 pipe, where every warp instruction
+// costs 16 cycles, and the kernels below test their flags in every thread.
+__device__ __forceinline__ bool flag_set(const double* sc, int slot) {
+  return (__double_as_longlong(sc[slot]) << 1) != 0;
+}
+// float -> double without the FP64 pipe (exact; the FP64 instance passes through)
+__device__ __forceinline__ double to_dbl(float x) { return widen_exact(x); }
+__device__ __forceinline__ double to_dbl(double x) { return x; }
+
 struct KrylovWork {
   int64_t N = 0;
   int pad = 0, m = 0, fp32 = -1;
@@ -315,7 +325,7 @@ __global__ void k_bicg_init(int64_t N, const double* __restrict__ rhs, T* x, T* 
 template <class T>
 __global__ void k_bicg_p(int64_t N, const double* __restrict__ sc, const T* __restrict__ r, T* p,
                          const T* __restrict__ v, const T* __restrict__ dinv, T* __restrict__ ph) {
-  if (sc[S_DONE] != 0.0) return;
+  if (flag_set(sc, S_DONE)) return;
   const T beta = (T)sc[S_BETA];       // (rho / rho_old)(alpha / omega), formed once by the previous kernel
   const T om = (T)sc[S_OMEGA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -330,7 +340,7 @@ template <int KT, class T>
 __global__ void k_bicg_spmv1(int64_t N, Offsets of, double* sc, const T* __restrict__ B, const T* __restrict__ x,
                              T* __restrict__ y, const T* __restrict__ a, double* __restrict__ part,
                              unsigned int* counter) {
-  if (sc[S_DONE] != 0.0) return;
+  if (flag_set(sc, S_DONE)) return;
   const int K = KT > 0 ? KT : of.K;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
@@ -355,7 +365,7 @@ template <class T>
 __global__ void k_bicg_s(int64_t N, double* sc, const T* __restrict__ r, const T* __restrict__ v,
                          const T* __restrict__ dinv, T* __restrict__ s, T* __restrict__ sh, double* __restrict__ part,
                          unsigned int* counter) {
-  if (sc[S_DONE] != 0.0) return;
+  if (flag_set(sc, S_DONE)) return;
   const T al = (T)sc[S_ALPHA];
   T a0 = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -416,7 +426,7 @@ __global__ void k_bicg_xr(int64_t N, double* sc, T* __restrict__ x, const T* __r
                           const T* __restrict__ sh, const T* __restrict__ s, const T* __restrict__ t,
                           T* __restrict__ r, const T* __restrict__ rh, double* __restrict__ part,
                           unsigned int* counter, GraphCond cond) {
-  if (sc[S_DONE] != 0.0) {
+  if (flag_set(sc, S_DONE)) {
     if (cond.use && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond.h, 0u);
     return;
   }
@@ -696,9 +706,9 @@ template <int KT, class T>
 __global__ void k_gm_residual(int64_t N, Offsets of, double* sc, const T* __restrict__ B, const T* __restrict__ x,
                               const double* __restrict__ rhs, T* __restrict__ w, double* __restrict__ part,
                               unsigned int* counter) {
-  if (sc[S_DONE] != 0.0) return;
+  if (flag_set(sc, S_DONE)) return;
   const int K = KT > 0 ? KT : of.K;
-  const bool first = sc[S_FIRST] != 0.0;
+  const bool first = flag_set(sc, S_FIRST);
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
   if (i < N) {
@@ -740,8 +750,11 @@ __global__ void k_gm_residual(int64_t N, Offsets of, double* sc, const T* __rest
 template <class T>
 __global__ void k_gm_normalize(int64_t N, const double* __restrict__ sc, const T* __restrict__ w, T* __restrict__ vk,
                                const T* __restrict__ dinv, T* __restrict__ z) {
-  if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
-  const T ih = (T)sc[S_INVH];
+  if (flag_set(sc, S_DONE) || flag_set(sc, S_CYCLE_DONE)) return;
+  __shared__ T ihs;   // one conversion per block instead of one per thread
+  if (threadIdx.x == 0) ihs = (T)sc[S_INVH];
+  __syncthreads();
+  const T ih = ihs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const T vi = w[i] * ih;
     vk[i] = vi;
@@ -752,7 +765,7 @@ __global__ void k_gm_normalize(int64_t N, const double* __restrict__ sc, const T
 template <int KT, class T>
 __global__ void k_gm_spmv(int64_t N, Offsets of, const double* __restrict__ sc, const T* __restrict__ B,
                           const T* __restrict__ z, T* __restrict__ w) {
-  if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
+  if (flag_set(sc, S_DONE) || flag_set(sc, S_CYCLE_DONE)) return;
   const int K = KT > 0 ? KT : of.K;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -781,9 +794,9 @@ template <class T, int QMAX>
 __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, int m, int hslot, int outslot,
                                                  T* __restrict__ w, const T* __restrict__ V, size_t vstride,
                                                  double* __restrict__ part, int64_t pstride, unsigned int* counter) {
-  if (sc[S_DONE] != 0.0 || sc[S_CYCLE_DONE] != 0.0) return;
+  if (flag_set(sc, S_DONE) || flag_set(sc, S_CYCLE_DONE)) return;
   const bool first = hslot < 0;                               // launch (1)
-  const bool no_reorth = !first && sc[S_NO_REORTH] != 0.0;
+  const bool no_reorth = !first && flag_set(sc, S_NO_REORTH);
   if (no_reorth && outslot < 0) return;                       // launch (3) has nothing to do
   const bool want_norm = outslot < 0 || no_reorth;
   if (want_norm && no_reorth) outslot = -1;
@@ -818,26 +831,28 @@ __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, i
   // sums: the k + 1 dots (and ||w||^2 as sum k + 1 in launch (1)), or the norm alone
   const int nq = want_norm ? 1 : (first ? k + 2 : k + 1);
   if (want_norm) {
-    const double t = block_allsum((double)nrm);
+    const double t = block_allsum(to_dbl(nrm));
     if (threadIdx.x == 0) part[blockIdx.x] = t;
   } else {
-    __shared__ double red[kBlock / 32][QMAX + 1];
+    // a block's warp sums meet in the vector type (for the single-precision instance: no
+    // FP64 instruction per warp and sum) and are widened once per block
+    __shared__ T red[kBlock / 32][QMAX + 1];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
       if (q > k) break;
       const T t = warp_sum(acc[q]);
-      if (lane == 0) red[wp][q] = (double)t;
+      if (lane == 0) red[wp][q] = t;
     }
     if (first) {
       const T t = warp_sum(nrm);
-      if (lane == 0) red[wp][k + 1] = (double)t;
+      if (lane == 0) red[wp][k + 1] = t;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-      double s = 0.0;
+      T s = 0;
       for (int u = 0; u < (int)(blockDim.x >> 5); ++u) s += red[u][q];
-      part[q * pstride + blockIdx.x] = s;
+      part[q * pstride + blockIdx.x] = to_dbl(s);
     }
   }
   __threadfence();   // every thread that wrote a partial makes it visible before the count

@@ -16,13 +16,13 @@
 //  1. k_mcp_split:   u -> pairs (integer pipe);
 //  2. k_mcp_rows:    per row, y = f - AG u and the bounds u_max, u_min over N_i in
 //                    one pass over the row's neighbours (the same state loads serve
-//                    both), A = u_max - u, B = u - u_min;
+//                    both), A = u_max - u, B = u - u_min; clears the clip mask;
 //  3. k_mcp_edges:   per pair i < j, the exact single-precision pre-test of mc.cu on
 //                    the high parts, and for the pairs it cannot clear, T_i, T_j and
-//                    c_ij in pair arithmetic (stored at row i), and every row's clip
-//                    mask (bit ku for a clipped pair);
+//                    c_ij in pair arithmetic (stored at row i, bit ku of row i's mask);
 //  4. k_mcp_residual: res = y - sum_j c_ij on free rows (0 on Dirichlet rows), in
-//                    pairs, rounded to double once; block partials of res^2.
+//                    pairs, rounded to double once; block partials of res^2, summed by
+//                    the last block when the caller wants the norm.
 // Accuracy: every value carries a relative error of at most 2^-48 and every product
 // and sum an error of that order relative to the magnitudes summed, so res agrees
 // with its FP64 evaluation to ~1e-14 of sum_j |AG_ij u_j| + sum_j |c_ij|, and the
@@ -44,7 +44,8 @@ template <int KT>
 __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
                                                      const float2* __restrict__ up, const float2* __restrict__ AGp,
                                                      const float2* __restrict__ fp, float2* __restrict__ yp,
-                                                     float2* __restrict__ abh, float2* __restrict__ abl) {
+                                                     float2* __restrict__ abh, float2* __restrict__ abl,
+                                                     unsigned int* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, cons
   if (Bh < 0.f) Bh = Bl = 0.f;
   abh[i] = make_float2(Ah, Bh);
   abl[i] = make_float2(Al, Bl);
+  clip[i] = 0u;
 }
 
 // The pre-test of mc.cu (k_mc_edges), on the high parts: T = 2|d| X - a |D| is
@@ -120,37 +122,34 @@ __device__ __forceinline__ void side_value(float d2h, float d2l, float xh, float
   two_sum(s, e, th, tl);
 }
 
-// Everything one pair slot (i, j = i + o) needs, loaded at once.  On the states the
-// fixed point produces nearly every warp has a pair the pre-test cannot clear, so the
-// low parts are read in the same round trip instead of a dependent second one.
-struct PairLoad {
-  float d2h, aih, ajh, d2l, ail, ajl;   // 2|d|, a_ij, a_ji: high and low parts
-  float2 ui, uj;                        // the states
-  float2 bhi, bhj, bli, blj;            // (A, B) high and low parts at i and j
-};
-
-// The clipped amount c_ij (c = -min(0, T_i, T_j) for r_ij > 0, min(0, T_i, T_j) for
-// r_ij < 0); returns false when the pair is not clipped.
-__device__ __forceinline__ bool pair_clip(const PairLoad& L, float2& c) {
-  const bool side_i = L.aih > 0.f, side_j = L.ajh > 0.f;
-  if (!(L.d2h > 0.f) || !(side_i || side_j)) return false;       // d = 0, or no side can clip
-  if (L.ui.x == L.uj.x && L.ui.y == L.uj.y) return false;         // u_i = u_j: r = 0
-  const bool rpos = pair_gt(L.ui.x, L.ui.y, L.uj.x, L.uj.y);      // r_ij = d (u_j - u_i) > 0  <=>  u_j < u_i
+// One pair (i, j = i + o) of row i given its loaded data; returns true and the clipped
+// amount c_ij (c = -min(0, T_i, T_j) for r_ij > 0, min(0, T_i, T_j) for r_ij < 0) when
+// the pair is clipped.  The low parts of 2|d|, a_ij, a_ji are loaded only here, for the
+// pairs the pre-test cannot clear.
+__device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __restrict__ pfl,
+                                          const float2* __restrict__ abl, int64_t i, int64_t j, float d2h, float aih,
+                                          float ajh, float2 ui, float2 uj, float2 bi, float2 bj, float2& c) {
+  const bool side_i = aih > 0.f, side_j = ajh > 0.f;
+  if (!(d2h > 0.f) || !(side_i || side_j)) return false;   // d = 0, or no side can clip
+  if (ui.x == uj.x && ui.y == uj.y) return false;           // u_i = u_j: r = 0
+  const bool rpos = pair_gt(ui.x, ui.y, uj.x, uj.y);        // r_ij = d (u_j - u_i) > 0  <=>  u_j < u_i
   // room of each side: r > 0 uses A_i = u_i^max - u_i and B_j; r < 0 uses B_i and A_j
-  const float xih = rpos ? L.bhi.x : L.bhi.y, xjh = rpos ? L.bhj.y : L.bhj.x;
-  if (L.ui.x != L.uj.x) {
-    const bool ok_i = !side_i || side_clear(L.d2h, L.aih, xih, L.ui.x, L.uj.x);
-    const bool ok_j = !side_j || side_clear(L.d2h, L.ajh, xjh, L.ui.x, L.uj.x);
+  const float xih = rpos ? bi.x : bi.y, xjh = rpos ? bj.y : bj.x;
+  if (ui.x != uj.x) {
+    const bool ok_i = !side_i || side_clear(d2h, aih, xih, ui.x, uj.x);
+    const bool ok_j = !side_j || side_clear(d2h, ajh, xjh, ui.x, uj.x);
     if (ok_i && ok_j) return false;
   }
-  const float xil = rpos ? L.bli.x : L.bli.y, xjl = rpos ? L.blj.y : L.blj.x;
+  const float d2l = __ldcs(pfl + q), ail = __ldcs(pfl + KN + q), ajl = __ldcs(pfl + 2 * KN + q);
+  const float2 li = abl[i], lj = abl[j];
+  const float xil = rpos ? li.x : li.y, xjl = rpos ? lj.y : lj.x;
   float Dh, Dl;   // |u_j - u_i|
-  if (rpos) pair_sub(L.ui.x, L.ui.y, L.uj.x, L.uj.y, Dh, Dl);
-  else pair_sub(L.uj.x, L.uj.y, L.ui.x, L.ui.y, Dh, Dl);
+  if (rpos) pair_sub(ui.x, ui.y, uj.x, uj.y, Dh, Dl);
+  else pair_sub(uj.x, uj.y, ui.x, ui.y, Dh, Dl);
   float mh = 0.f, ml = 0.f;   // min(0, T_i, T_j)
   if (side_i) {
     float th, tl;
-    side_value(L.d2h, L.d2l, xih, xil, L.aih, L.ail, Dh, Dl, th, tl);
+    side_value(d2h, d2l, xih, xil, aih, ail, Dh, Dl, th, tl);
     if (pair_gt(mh, ml, th, tl)) {
       mh = th;
       ml = tl;
@@ -158,7 +157,7 @@ __device__ __forceinline__ bool pair_clip(const PairLoad& L, float2& c) {
   }
   if (side_j) {
     float th, tl;
-    side_value(L.d2h, L.d2l, xjh, xjl, L.ajh, L.ajl, Dh, Dl, th, tl);
+    side_value(d2h, d2l, xjh, xjl, ajh, ajl, Dh, Dl, th, tl);
     if (pair_gt(mh, ml, th, tl)) {
       mh = th;
       ml = tl;
@@ -169,12 +168,11 @@ __device__ __forceinline__ bool pair_clip(const PairLoad& L, float2& c) {
   return true;
 }
 
-// Clipped amount c_ij of every pair i < j (stored at row i, only where nonzero) and
-// every row's clip mask (bit ku: the pair with upper offset ku is clipped), one thread
-// per pair slot (ku, i): a block covers 32 consecutive rows (threadIdx.x) and all
-// upper offsets (threadIdx.y).  The 2|d|, k_ij, k_ji data are read once per sweep and
-// streamed past L2, so that the node arrays (gathered at i and at i + o) stay there;
-// the masks meet in shared memory and are stored whole, one word per row.
+// Clipped amount c_ij of every pair i < j (stored at row i, only where nonzero; the
+// row's clip mask gets bit ku), one thread per pair slot (ku, i): a block covers 32
+// consecutive rows (threadIdx.x) and all upper offsets (threadIdx.y).  Every load a
+// pair needs for its pre-test is issued at once (one round trip to memory); only the
+// pairs the pre-test cannot clear load the low parts.
 template <int KT>
 __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf, const float* __restrict__ pfl,
                             const float2* __restrict__ up, const float2* __restrict__ abh,
@@ -183,34 +181,55 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf,
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   const int ku = threadIdx.y;
   const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
-  __shared__ unsigned int smask[32];
-  if (ku == 0) smask[threadIdx.x] = 0u;
+  if (i >= N) return;
+  const int64_t q = (int64_t)ku * N + i;
+  const int64_t j = i + of.o[Kup + 1 + ku];
+  const int64_t KN = (int64_t)Kup * N;
+  // 2|d|, a_ij, a_ji (high parts), streamed past L2 so that the node arrays stay there
+  const float d2h = __ldcs(pf + q), aih = __ldcs(pf + KN + q), ajh = __ldcs(pf + 2 * KN + q);
+  const float2 ui = up[i], uj = up[j];
+  const float2 bi = abh[i], bj = abh[j];
+  float2 c;
+  if (pair_clip(q, KN, pfl, abl, i, j, d2h, aih, ajh, ui, uj, bi, bj, c)) {
+    c_up[q] = c;
+    atomicOr(clip + i, 1u << ku);
+  }
+}
+
+// ||res||^2 from the block partials, by the block that finishes last (the blocks count
+// themselves on `count`, which that block resets).  The 256 threads take the roles of
+// the 1024 threads of k_finalize_sum (thread t those of t, t + 256, t + 512, t + 768:
+// the same strided sums, the same shuffle trees over the same lanes, the same warp
+// order), so the total is that kernel's bit for bit and the host-driven loop and the
+// graph (whose control kernel sums the partials the same way) stop alike.
+__device__ __forceinline__ void last_block_normsq(const double* part, unsigned int* count, double* out) {
+  __shared__ bool last;
+  __threadfence();
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
   __syncthreads();
-  if (i < N) {
-    const int64_t q = (int64_t)ku * N + i;
-    const int64_t j = i + of.o[Kup + 1 + ku];
-    const int64_t KN = (int64_t)Kup * N;
-    PairLoad L;
-    L.d2h = __ldcs(pf + q);
-    L.aih = __ldcs(pf + KN + q);
-    L.ajh = __ldcs(pf + 2 * KN + q);
-    L.d2l = __ldcs(pfl + q);
-    L.ail = __ldcs(pfl + KN + q);
-    L.ajl = __ldcs(pfl + 2 * KN + q);
-    L.ui = up[i];
-    L.uj = up[j];
-    L.bhi = abh[i];
-    L.bhj = abh[j];
-    L.bli = abl[i];
-    L.blj = abl[j];
-    float2 c;
-    if (pair_clip(L, c)) {
-      c_up[q] = c;
-      atomicOr(smask + threadIdx.x, 1u << ku);
+  if (!last) return;
+  __threadfence();
+  const int n = gridDim.x;
+  double v[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v[m] = 0.0;
+    for (int q = threadIdx.x + 256 * m; q < n; q += 1024) v[m] += __ldcg(part + q);
+    v[m] = warp_sum(v[m]);
+  }
+  __shared__ double sw[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) sw[w + 8 * m] = v[m];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const double t = warp_sum(sw[lane]);
+    if (lane == 0) {
+      *out = t;
+      *count = 0u;
     }
   }
-  __syncthreads();
-  if (ku == 0 && i < N) clip[i] = smask[threadIdx.x];
 }
 
 template <int KT>
@@ -218,7 +237,8 @@ __global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, 
                                                          const unsigned int* __restrict__ clip,
                                                          const float2* __restrict__ c_up,
                                                          const float2* __restrict__ yp, const uint8_t* __restrict__ dir,
-                                                         double* __restrict__ res, double* __restrict__ part) {
+                                                         double* __restrict__ res, double* __restrict__ part,
+                                                         unsigned int* __restrict__ count, double* __restrict__ normsq) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double r2 = 0.0;
@@ -282,6 +302,7 @@ __global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, 
     res[i] = rv;
   }
   block_sum_to(r2, part);
+  if (normsq) last_block_normsq(part, count, normsq);
 }
 
 // Pair copies of the stationary operator data (once, at assembly): AG, f and, per pair,
@@ -310,7 +331,7 @@ int mc_pair_setup(afc_problem_s* p) {
   int st;
   if ((st = p->AGp.alloc(p->K * N)) || (st = p->fp2.alloc(N, p->pad)) || (st = p->pairf_lo.alloc(3 * p->Kup * N)) ||
       (st = p->up2.alloc(N, p->pad)) || (st = p->abh2.alloc(N, p->pad)) || (st = p->abl2.alloc(N, p->pad)) ||
-      (st = p->yp2.alloc(N, p->pad)) ||
+      (st = p->yp2.alloc(N, p->pad)) || (st = p->fin_count.alloc(1)) ||
       (st = p->cp_up.alloc(p->Kup * N)))
     return st;
   AFC_LAUNCH(p, "k_mcp_setup", k_mcp_setup<<<grid_for(N), kBlock, 0, p->stream>>>(
@@ -328,16 +349,16 @@ int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
     AFC_LAUNCH(p, "k_mcp_rows", k_mcp_rows<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->up2.p, p->AGp.p,
-                                                                     p->fp2.p, p->yp2.p, p->abh2.p, p->abl2.p));
+                                                                     p->fp2.p, p->yp2.p, p->abh2.p, p->abl2.p,
+                                                                     p->clip.p));
     if (limiter == AFC_LIM_MC)
       AFC_LAUNCH(p, "k_mcp_edges", k_mcp_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(
                                        N, p->offs, p->pairf.p, p->pairf_lo.p, p->up2.p, p->abh2.p, p->abl2.p,
                                        p->cp_up.p, p->clip.p));
     AFC_LAUNCH(p, "k_mcp_residual", k_mcp_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->clip.p,
                                                                              p->cp_up.p, p->yp2.p, p->dir.p, res,
-                                                                             p->part.p));
+                                                                             p->part.p, p->fin_count.p, normsq_slot));
   });
-  if (normsq_slot) finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
