@@ -152,7 +152,7 @@ struct afc_problem_s {
   afc::DBuf<double> u, u0, ustage, udot, ut, Rp, Rm, Fs, Qp, Qm, b0, res, delta, umax, umin, tmp, cn_a, cn_s;
   afc::DBuf<double> bA, bB;         // MC: u_max - u and u - u_min
   afc::DBuf<double> Fold;           // CN with the MC limiter: F*(u^{n-1})
-  afc::DBuf<unsigned int> clip;     // MC: per row, bit ku set if the pair (i, i + o) was clipped
+  afc::DBuf<unsigned long long> clip;   // MC: per row, bit k set if the pair of offset k was clipped
   afc::DBuf<float4> nodef;          // MC: (u, u_max - u, u - u_min) rounded to single
   // MC, mixed precision: the sweep in float pairs (mc_pair.cu)
   afc::DBuf<float2> AGp, fp2;       // K * N and N: AG and f as pairs

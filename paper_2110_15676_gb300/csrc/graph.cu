@@ -46,9 +46,7 @@ __global__ void k_fp_init(double* sc, double thresh, int fixed, int maxit) {
 // (the order of finalize_sum) before the decision, so the sum needs no launch of its own.
 __global__ void k_fp_control(double* sc, const double* __restrict__ part, int npart,
                              cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_solve) {
-  double v = 0.0;
-  for (int q = threadIdx.x; q < npart; q += blockDim.x) v += part[q];
-  block_sum_to(v, sc + F_NORMSQ);   // a single block: sc[F_NORMSQ]
+  block_sum_to(strided_sum_1024(part, npart, threadIdx.x), sc + F_NORMSQ);   // one block of 1024
   if (threadIdx.x != 0) return;
   const double R = sqrt(sc[F_NORMSQ]);
   const double it = sc[F_CORR];

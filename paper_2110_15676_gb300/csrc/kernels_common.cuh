@@ -50,16 +50,21 @@ __device__ __forceinline__ double neg_bits(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
 }
 
-// Exact float -> double on the integer pipe (zero and subnormal floats give a
-// signed zero; every user of a flux widens it the same way, so P+/- and F* see
-// the same values).
+// Exact float -> double on the integer pipe (every user of a flux widens it the same
+// way, so P+/- and F* see the same values).  A subnormal float m * 2^-149 becomes the
+// normal double 2^(p - 149) (m / 2^p), p the position of m's leading bit.
 __device__ __forceinline__ double widen_exact(float x) {
   const unsigned b = __float_as_uint(x);
-  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
   const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
+  if (e == 0u) {
+    if (m == 0u) return __longlong_as_double((long long)s);
+    const unsigned p = 31u - (unsigned)__clz(m);   // 0 .. 22
+    return __longlong_as_double(
+        (long long)(s | ((unsigned long long)(p + 874u) << 52) | ((unsigned long long)(m ^ (1u << p)) << (52u - p))));
+  }
   const unsigned long long de = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
-  const unsigned long long bits = e == 0u ? s : (s | (de << 52) | ((unsigned long long)(b & 0x7fffffu) << 29));
-  return __longlong_as_double((long long)bits);
+  return __longlong_as_double((long long)(s | (de << 52) | ((unsigned long long)m << 29)));
 }
 
 // Sums of the positive and of the negative values of a row's pair fluxes, exact:
@@ -236,6 +241,24 @@ __device__ __forceinline__ double warp0_column_sum(const double* col) {
   double t = col[lane];
   for (int w = lane + 32; w < (int)blockDim.x; w += 32) t += col[w];
   return warp_sum(t);
+}
+
+// The final sums over a pass's block partials run as 1024 threads: thread t adds
+// part[t], part[t + 1024], part[t + 2048], ... (q < n) from left to right, then the
+// block sums the threads (block_sum_to).  This is thread t's sum; its loads go out
+// eight at a time instead of one round trip each.  A slot past n adds +0.0, which
+// leaves the sum unchanged (it starts at +0.0, so it is never -0.0).  The loads go
+// through L2 (partials of other blocks of the same grid are read this way too).
+__device__ __forceinline__ double strided_sum_1024(const double* part, int n, int t) {
+  double v = 0.0;
+  for (int q0 = t; q0 < n; q0 += 8 * 1024) {
+    double x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = q0 + 1024 * m < n ? __ldcg(part + q0 + 1024 * m) : 0.0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v += x[m];
+  }
+  return v;
 }
 
 // Sum v over the block and store it in part[blockIdx.x].

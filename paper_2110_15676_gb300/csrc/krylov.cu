@@ -62,9 +62,7 @@ template struct DBuf<float2>;
 namespace {
 
 __global__ void k_finalize_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
-  double v = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) v += part[q];
-  block_sum_to(v, out);   // one block: out[0]
+  block_sum_to(strided_sum_1024(part, n, threadIdx.x), out);   // one block of 1024: out[0]
 }
 
 }  // namespace

@@ -29,7 +29,7 @@ template <int KT>
 __global__ void k_mc_bounds(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
                             const double* __restrict__ u, double* __restrict__ umax, double* __restrict__ umin,
                             double* __restrict__ bA, double* __restrict__ bB, float4* __restrict__ nf,
-                            unsigned int* __restrict__ clip) {
+                            unsigned long long* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -55,12 +55,13 @@ __global__ void k_mc_bounds(int64_t N, Offsets of, const unsigned long long* __r
   const float uf = __double2float_rn(ui);
   const bool exact = __double_as_longlong(widen_exact(uf)) == __double_as_longlong(ui);
   nf[i] = make_float4(uf, (float)A, (float)B, exact ? 1.f : 0.f);
-  clip[i] = 0u;
+  clip[i] = 0ull;
 }
 
 // Clipped amount c_ij of every pair i < j (stored at row i, only where nonzero; the
-// row's clip mask gets bit ku) for one thread per pair slot (ku, i): a block covers
-// 32 consecutive rows (threadIdx.x) and all upper offsets (threadIdx.y).
+// clip masks of rows i and j get the pair's offset bits) for one thread per pair slot
+// (ku, i): a block covers 32 consecutive rows (threadIdx.x) and all upper offsets
+// (threadIdx.y).
 //
 // Exact pre-test.  A side T = 2|d| X - a |D| (a > 0) can only clip if T < 0.  The
 // test first evaluates T from single-precision copies of 2|d|, a, u and X together
@@ -86,7 +87,7 @@ __global__ void k_mc_edges(int64_t N, Offsets of, const double* __restrict__ d2_
                            const double* __restrict__ kji, const float* __restrict__ pf,
                            const double* __restrict__ u, const double* __restrict__ bA,
                            const double* __restrict__ bB, const float4* __restrict__ nf, double* __restrict__ c_up,
-                           unsigned int* __restrict__ clip) {
+                           unsigned long long* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   const int ku = threadIdx.y;
   const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
@@ -116,7 +117,10 @@ __global__ void k_mc_edges(int64_t N, Offsets of, const double* __restrict__ d2_
   if (side_j) m = imin(m, fma(-kji[q], absD, d2 * (rpos ? bB[j] : bA[j])));
   if (!is0(m)) {
     c_up[q] = rpos ? neg_bits(m) : m;
-    atomicOr(clip + i, 1u << ku);
+    // the pair's bit at both ends: offset index Kup + 1 + ku at row i, Kup - 1 - ku
+    // (the offset -o back to i) at row j
+    atomicOr(clip + i, 1ull << (Kup + 1 + ku));
+    atomicOr(clip + j, 1ull << (Kup - 1 - ku));
   }
 }
 
@@ -125,7 +129,7 @@ __global__ void k_mc_edges(int64_t N, Offsets of, const double* __restrict__ d2_
 // With Fout, also F*_i = sum_j (d_ij (u_j - u_i) - c_ij) for inspection.
 template <int KT>
 __global__ void k_mc_residual(int64_t N, Offsets of, int limiter, const unsigned long long* __restrict__ mask,
-                              const unsigned int* __restrict__ clip, const double* __restrict__ c_up,
+                              const unsigned long long* __restrict__ clip, const double* __restrict__ c_up,
                               const double* __restrict__ Mop,
                               const double* __restrict__ d_up, const double* __restrict__ u,
                               const double* __restrict__ f, const uint8_t* __restrict__ dir,
@@ -142,10 +146,7 @@ __global__ void k_mc_residual(int64_t N, Offsets of, int limiter, const unsigned
       double C = 0.0;
       if (limiter == AFC_LIM_MC) {
         // pairs with a nonzero clipped amount: bit k of `bits` for offset index k
-        unsigned long long bits = (unsigned long long)clip[i] << (Kup + 1);
-#pragma unroll
-        for (int ku = 0; ku < Kup; ++ku)
-          bits |= (unsigned long long)((clip[i - of.o[Kup + 1 + ku]] >> ku) & 1u) << (Kup - 1 - ku);
+        unsigned long long bits = clip[i];
         while (bits) {
           const int k = __ffsll(bits) - 1;
           bits &= bits - 1;

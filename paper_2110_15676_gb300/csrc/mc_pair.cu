@@ -19,10 +19,12 @@
 //                    both), A = u_max - u, B = u - u_min; clears the clip mask;
 //  3. k_mcp_edges:   per pair i < j, the exact single-precision pre-test of mc.cu on
 //                    the high parts, and for the pairs it cannot clear, T_i, T_j and
-//                    c_ij in pair arithmetic (stored at row i, bit ku of row i's mask);
+//                    c_ij in pair arithmetic (stored at row i, its bit set in the masks
+//                    of rows i and j);
 //  4. k_mcp_residual: res = y - sum_j c_ij on free rows (0 on Dirichlet rows), in
-//                    pairs, rounded to double once; block partials of res^2, summed by
-//                    the last block when the caller wants the norm.
+//                    pairs, rounded to double once; block partials of res^2 (in pairs
+//                    while |res| < 2^60), summed by the last block when the caller
+//                    wants the norm.
 // Accuracy: every value carries a relative error of at most 2^-48 and every product
 // and sum an error of that order relative to the magnitudes summed, so res agrees
 // with its FP64 evaluation to ~1e-14 of sum_j |AG_ij u_j| + sum_j |c_ij|, and the
@@ -35,7 +37,17 @@ namespace afc {
 
 namespace {
 
+// Programmatic dependent launch between the passes of a sweep: a pass lets the next
+// one launch as soon as all of its blocks run (griddepcontrol.launch_dependents), and
+// the next pass issues the loads of data no earlier pass writes (the matrix, the pair
+// coefficients, the Dirichlet mask) before it waits for its predecessor's results
+// (griddepcontrol.wait), so those loads overlap the predecessor's last wave.  Launched
+// without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __global__ void k_mcp_split(int64_t N, const double* __restrict__ u, float2* __restrict__ up) {
+  pdl_trigger();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < N) up[i] = split_pair(u[i]);
 }
@@ -45,24 +57,28 @@ __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, cons
                                                      const float2* __restrict__ up, const float2* __restrict__ AGp,
                                                      const float2* __restrict__ fp, float2* __restrict__ yp,
                                                      float2* __restrict__ abh, float2* __restrict__ abl,
-                                                     unsigned int* __restrict__ clip) {
+                                                     unsigned long long* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K;
+  pdl_trigger();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
+  // the row's matrix entries, mask and source first (no pass writes them), then, once
+  // the split is done, its states: all loads of the row in flight together
   const unsigned long long mk = __ldcs(mask + i);
-  const float2 ui = up[i];
-  float mxh = ui.x, mxl = ui.y, mnh = ui.x, mnl = ui.y;
   const float2 f = __ldcs(fp + i);
-  float sh = f.x, sl = f.y;   // y = f - sum_k AG_ik u_{i + o_k}: running high sum, summed errors
-  // all loads of the row first, so that they are in flight together
   constexpr int KL = KT > 0 ? KT : 1;
   float2 vv[KL], aa[KL];
   if (KT > 0) {
 #pragma unroll
-    for (int k = 0; k < KL; ++k) {
-      vv[k] = up[i + of.o[k]];
-      aa[k] = __ldcs(AGp + (int64_t)k * N + i);   // read once per sweep: keep it out of L2
-    }
+    for (int k = 0; k < KL; ++k) aa[k] = __ldcs(AGp + (int64_t)k * N + i);   // read once per sweep: past L2
+  }
+  pdl_wait();
+  const float2 ui = up[i];
+  float mxh = ui.x, mxl = ui.y, mnh = ui.x, mnl = ui.y;
+  float sh = f.x, sl = f.y;   // y = f - sum_k AG_ik u_{i + o_k}: running high sum, summed errors
+  if (KT > 0) {
+#pragma unroll
+    for (int k = 0; k < KL; ++k) vv[k] = up[i + of.o[k]];
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -94,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, cons
   if (Bh < 0.f) Bh = Bl = 0.f;
   abh[i] = make_float2(Ah, Bh);
   abl[i] = make_float2(Al, Bl);
-  clip[i] = 0u;
+  clip[i] = 0ull;
 }
 
 // The pre-test of mc.cu (k_mc_edges), on the high parts: T = 2|d| X - a |D| is
@@ -169,30 +185,37 @@ __device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __
 }
 
 // Clipped amount c_ij of every pair i < j (stored at row i, only where nonzero; the
-// row's clip mask gets bit ku), one thread per pair slot (ku, i): a block covers 32
-// consecutive rows (threadIdx.x) and all upper offsets (threadIdx.y).  Every load a
-// pair needs for its pre-test is issued at once (one round trip to memory); only the
-// pairs the pre-test cannot clear load the low parts.
+// clip masks of rows i and j get the pair's offset bits, so that the residual pass
+// finds a row's clipped pairs in its own mask), one thread per pair slot (ku, i): a
+// block covers 32 consecutive rows (threadIdx.x) and all upper offsets (threadIdx.y).
+// Every load a pair needs for its pre-test is issued at once (one round trip to
+// memory); only the pairs the pre-test cannot clear load the low parts.
 template <int KT>
 __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf, const float* __restrict__ pfl,
                             const float2* __restrict__ up, const float2* __restrict__ abh,
                             const float2* __restrict__ abl, float2* __restrict__ c_up,
-                            unsigned int* __restrict__ clip) {
+                            unsigned long long* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  pdl_trigger();
   const int ku = threadIdx.y;
   const int64_t i = blockIdx.x * (int64_t)32 + threadIdx.x;
   if (i >= N) return;
   const int64_t q = (int64_t)ku * N + i;
   const int64_t j = i + of.o[Kup + 1 + ku];
   const int64_t KN = (int64_t)Kup * N;
-  // 2|d|, a_ij, a_ji (high parts), streamed past L2 so that the node arrays stay there
+  // 2|d|, a_ij, a_ji (high parts), streamed past L2 so that the node arrays stay there;
+  // no pass writes them, so they load before the wait for the rows pass
   const float d2h = __ldcs(pf + q), aih = __ldcs(pf + KN + q), ajh = __ldcs(pf + 2 * KN + q);
+  pdl_wait();
   const float2 ui = up[i], uj = up[j];
   const float2 bi = abh[i], bj = abh[j];
   float2 c;
   if (pair_clip(q, KN, pfl, abl, i, j, d2h, aih, ajh, ui, uj, bi, bj, c)) {
     c_up[q] = c;
-    atomicOr(clip + i, 1u << ku);
+    // the pair's bit at both ends: offset index Kup + 1 + ku at row i, Kup - 1 - ku
+    // (the offset -o back to i) at row j
+    atomicOr(clip + i, 1ull << (Kup + 1 + ku));
+    atomicOr(clip + j, 1ull << (Kup - 1 - ku));
   }
 }
 
@@ -204,19 +227,18 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf,
 // graph (whose control kernel sums the partials the same way) stop alike.
 __device__ __forceinline__ void last_block_normsq(const double* part, unsigned int* count, double* out) {
   __shared__ bool last;
-  __threadfence();
-  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {   // the thread that stored the block's partial publishes it, then counts
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
   if (!last) return;
-  __threadfence();
+  if (threadIdx.x == 0) __threadfence();
+  __syncthreads();
   const int n = gridDim.x;
   double v[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    v[m] = 0.0;
-    for (int q = threadIdx.x + 256 * m; q < n; q += 1024) v[m] += __ldcg(part + q);
-    v[m] = warp_sum(v[m]);
-  }
+  for (int m = 0; m < 4; ++m) v[m] = warp_sum(strided_sum_1024(part, n, threadIdx.x + 256 * m));
   __shared__ double sw[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0)
@@ -234,25 +256,25 @@ __device__ __forceinline__ void last_block_normsq(const double* part, unsigned i
 
 template <int KT>
 __global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, int limiter,
-                                                         const unsigned int* __restrict__ clip,
+                                                         const unsigned long long* __restrict__ clip,
                                                          const float2* __restrict__ c_up,
                                                          const float2* __restrict__ yp, const uint8_t* __restrict__ dir,
                                                          double* __restrict__ res, double* __restrict__ part,
                                                          unsigned int* __restrict__ count, double* __restrict__ normsq) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double r2 = 0.0;
+  const bool isdir = i < N && dir[i];
+  pdl_wait();
+  float qh = 0.f, ql = 0.f;   // res^2 as an unnormalised pair
+  bool big = false;           // |res| >= 2^60: the block sums res^2 in double
+  double rv = 0.0;
   if (i < N) {
-    double rv = 0.0;
-    if (!dir[i]) {
+    if (!isdir) {
       const float2 y = __ldcs(yp + i);
       float sh = y.x, sl = y.y;
       if (limiter == AFC_LIM_MC) {
         // pairs with a clipped amount: bit k of `bits` for offset index k
-        unsigned long long bits = (unsigned long long)clip[i] << (Kup + 1);
-#pragma unroll
-        for (int ku = 0; ku < Kup; ++ku)
-          bits |= (unsigned long long)((clip[i - of.o[Kup + 1 + ku]] >> ku) & 1u) << (Kup - 1 - ku);
+        unsigned long long bits = clip[i];
         if (KT > 0) {
           // every clipped amount of the row loaded at once (predicated), then summed in
           // offset order: res -= c_ij, with c_ij the stored amount of an upper pair
@@ -297,11 +319,44 @@ __global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, 
       float h, l;
       two_sum(sh, sl, h, l);
       rv = widen_exact(h) + widen_exact(l);
-      r2 = rv * rv;
+      big = !(fabsf(h) < 1.152921504606846976e18f);   // 2^60 (and NaN)
+      float e;
+      two_prod(h, h, qh, e);
+      ql = __fmaf_rn(__fadd_rn(h, h), l, e);
     }
     res[i] = rv;
   }
-  block_sum_to(r2, part);
+  // the block's sum of res^2 in pairs: the threads' pairs by columns in warp 0, as
+  // block_sum_to does in double; with a |res| >= 2^60 in the block (res^2 near the
+  // float range), in double by block_sum_to
+  __shared__ float2 sq[kBlock];
+  sq[threadIdx.x] = make_float2(qh, ql);
+  if (__syncthreads_or(big)) {
+    block_sum_to(rv * rv, part);
+  } else if (threadIdx.x < 32) {
+    float th = 0.f, tl = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) {
+      const float2 v = sq[threadIdx.x + 32 * w];
+      float s, e;
+      two_sum(th, v.x, s, e);
+      th = s;
+      tl = __fadd_rn(tl, __fadd_rn(e, v.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_down_sync(0xffffffffu, th, o), ol = __shfl_down_sync(0xffffffffu, tl, o);
+      float s, e;
+      two_sum(th, oh, s, e);
+      th = s;
+      tl = __fadd_rn(tl, __fadd_rn(e, ol));
+    }
+    if (threadIdx.x == 0) {
+      float h, l;
+      two_sum(th, tl, h, l);
+      part[blockIdx.x] = widen_exact(h) + widen_exact(l);
+    }
+  }
   if (normsq) last_block_normsq(part, count, normsq);
 }
 
@@ -341,24 +396,57 @@ int mc_pair_setup(afc_problem_s* p) {
   return AFC_OK;
 }
 
+namespace {
+// A pass of the sweep, launched with programmatic dependent launch on `pdl`.
+template <class... KArgs, class... Args>
+cudaError_t launch_pass(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+}  // namespace
+
 int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot) {
   const int64_t N = p->N;
   const int64_t g = grid_for(N);
   cudaStream_t s = p->stream;
+  // programmatic dependent launch between the passes, except while a graph is being
+  // captured (the solve's graphs keep plain launches)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  AFC_CUDA(cudaStreamIsCapturing(s, &cap));
+  const bool pdl = cap == cudaStreamCaptureStatusNone;
   AFC_LAUNCH(p, "k_mcp_split", k_mcp_split<<<g, kBlock, 0, s>>>(N, u, p->up2.p));
+  AFC_CUDA(cudaGetLastError());
+  int st = AFC_OK;
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
-    AFC_LAUNCH(p, "k_mcp_rows", k_mcp_rows<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->up2.p, p->AGp.p,
-                                                                     p->fp2.p, p->yp2.p, p->abh2.p, p->abl2.p,
-                                                                     p->clip.p));
-    if (limiter == AFC_LIM_MC)
-      AFC_LAUNCH(p, "k_mcp_edges", k_mcp_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(
-                                       N, p->offs, p->pairf.p, p->pairf_lo.p, p->up2.p, p->abh2.p, p->abl2.p,
-                                       p->cp_up.p, p->clip.p));
-    AFC_LAUNCH(p, "k_mcp_residual", k_mcp_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->clip.p,
-                                                                             p->cp_up.p, p->yp2.p, p->dir.p, res,
-                                                                             p->part.p, p->fin_count.p, normsq_slot));
+    cudaError_t e;
+    AFC_LAUNCH(p, "k_mcp_rows", e = launch_pass(pdl, k_mcp_rows<KT>, dim3((unsigned)g), dim3(kBlock), s, N, p->offs,
+                                                (const unsigned long long*)p->mask.p, (const float2*)p->up2.p,
+                                                (const float2*)p->AGp.p, (const float2*)p->fp2.p, p->yp2.p, p->abh2.p,
+                                                p->abl2.p, p->clip.p));
+    if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_rows"); return; }
+    if (limiter == AFC_LIM_MC) {
+      AFC_LAUNCH(p, "k_mcp_edges",
+                 e = launch_pass(pdl, k_mcp_edges<KT>, dim3((unsigned)grid_for(N, 32)), dim3(32, p->Kup), s, N, p->offs,
+                                 (const float*)p->pairf.p, (const float*)p->pairf_lo.p, (const float2*)p->up2.p,
+                                 (const float2*)p->abh2.p, (const float2*)p->abl2.p, p->cp_up.p, p->clip.p));
+      if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_edges"); return; }
+    }
+    AFC_LAUNCH(p, "k_mcp_residual",
+               e = launch_pass(pdl, k_mcp_residual<KT>, dim3((unsigned)g), dim3(kBlock), s, N, p->offs, limiter,
+                               (const unsigned long long*)p->clip.p, (const float2*)p->cp_up.p, (const float2*)p->yp2.p,
+                               (const uint8_t*)p->dir.p, res, p->part.p, p->fin_count.p, normsq_slot));
+    if (e != cudaSuccess) st = cuda_fail(e, "launch k_mcp_residual");
   });
+  if (st) return st;
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }

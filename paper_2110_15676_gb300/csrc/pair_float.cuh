@@ -6,7 +6,8 @@
 // roofline.  A float pair carries 48 significand bits: a double rounded to a pair
 // (hi = RN(x), lo = RN(x - hi)) is within 2^-48 |x|, and products and sums of pairs
 // built from the error-free transformations below keep errors of that order
-// relative to the magnitudes involved, on a pipe 64 times faster.
+// relative to the magnitudes involved, on a pipe 64 times faster (down to 2^-126 in
+// magnitude; below, the floats' subnormal spacing 2^-149 bounds the absolute error).
 //
 // Error-free transformations, restated from their published definitions:
 //  * two_sum: Knuth's TwoSum (The Art of Computer Programming, vol. 2, 4.2.2):
@@ -59,33 +60,65 @@ __device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl,
   pl = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
 }
 
-// Rare doubles (zero excepted) whose high part is not a normal float, or whose low
-// part would be: kept out of line so that its FP64 instructions issue only for the
-// warps that need them.
+// Doubles of magnitude 2^127 or more, Inf and NaN, beyond the range of float pairs:
+// kept out of line so that its FP64 instructions issue only for the warps that need
+// them.
 __device__ __noinline__ float2 split_pair_fp64(double x) {
   const float h = __double2float_rn(x);
   return make_float2(h, __double2float_rn(x - (double)h));
 }
 
-// hi = RN(x), lo = RN(x - hi) (round to nearest, ties to even), on the integer pipe
-// for 2^-74 <= |x| < 2^127 and for zeros; other values take split_pair_fp64.
-// With e the biased exponent of x, the low 29 bits of its significand are what the
-// float drops; rounding adds one unit to the kept bits (a carry may move into the
-// exponent), and x - hi = (dropped bits - carry * 2^29) * 2^(e - 1075), an integer
-// of at most 29 bits times a power of two that is a normal float in that range.
+// hi = RN(x), lo = RN(x - hi) (round to nearest, ties to even) on the integer pipe, for
+// |x| < 2^127.  With e the biased exponent of x, the low 29 bits of its
+// significand are what the float drops; rounding adds one unit to the kept bits (a
+// carry may move into the exponent), and x - hi = r * 2^(e - 1075) with r = dropped
+// bits - carry * 2^29, an integer of at most 29 bits.  Where that value is a normal
+// float or a multiple of 2^-149 (e >= 926), it is rounded once, by the conversion of r
+// to float, and scaled exactly (by 2^(e - 1075), or by 2^-100 * 2^(e - 975) so that
+// every factor is a normal float).  Otherwise it is subnormal and not a multiple of
+// 2^-149: r is shifted to units of 2^-149 and rounded in integers, as is x itself when
+// |x| < 2^-126.  |x| >= 2^127 (and Inf, NaN) take split_pair_fp64.
 __device__ __forceinline__ float2 split_pair(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  if ((b << 1) == 0ull) return make_float2(__uint_as_float((unsigned)(b >> 32)), 0.f);
-  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-  if (e - 949u > 200u) return split_pair_fp64(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if (e < 897u) {   // |x| < 2^-126: hi is subnormal (or 0) and lo = 0, as |x - hi| <= 2^-150
+    unsigned q = 0;   // RN(|x| / 2^-149), 0 for |x| < 2^-151
+    if (e >= 872u) {
+      const unsigned sh = 926u - e;   // 30 .. 54
+      const unsigned long long sig = (b & 0xfffffffffffffull) | (1ull << 52);
+      const unsigned long long rb = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+      q = (unsigned)(sig >> sh);
+      q += (rb > half) | ((rb == half) & (q & 1u));
+    }
+    return make_float2(__uint_as_float(sign | q), 0.f);
+  }
+  if (e > 1149u) return split_pair_fp64(x);
   const unsigned rem = (unsigned)b & 0x1fffffffu;
   unsigned t = (unsigned)(((b >> 29) & 0x3ffffffffull) - (896ull << 23));
   const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (t & 1u));
   t += up;
   const int r = (int)rem - (int)(up << 29);
-  const float l = __fmul_rn(__int2float_rn(r), __uint_as_float((e - 948u) << 23));
-  return make_float2(__uint_as_float(sign | t), __uint_as_float(__float_as_uint(l) ^ sign));
+  const unsigned m = r < 0 ? (unsigned)(-r) : (unsigned)r;
+  bool normal = e >= 926u;   // lo = r * 2^(e - 1075) is a multiple of 2^-149, or normal
+  unsigned sh = 0;
+  if (!normal) {
+    sh = 926u - e;                      // 1 .. 29: |lo| = m * 2^-sh units of 2^-149
+    normal = (m >> sh) >= 0x800000u;    // |lo| >= 2^-126
+  }
+  unsigned lb;
+  if (normal) {
+    const bool low = e < 949u;
+    const float s1 = low ? 7.888609052210118e-31f : 1.f;                  // 2^-100
+    const float s2 = __uint_as_float((low ? e - 848u : e - 948u) << 23);  // 2^(e - 975) or 2^(e - 1075)
+    lb = __float_as_uint(__fmul_rn(__fmul_rn(__int2float_rn(r), s1), s2));
+  } else {
+    unsigned q = m >> sh;
+    const unsigned rb = m & ((1u << sh) - 1u), half = 1u << (sh - 1u);
+    q += (rb > half) | ((rb == half) & (q & 1u));
+    lb = q | (r < 0 ? 0x80000000u : 0u);   // the bit pattern of q * 2^-149 (q <= 2^23)
+  }
+  return make_float2(__uint_as_float(sign | t), __uint_as_float(lb ^ sign));
 }
 
 }  // namespace afc
