@@ -160,7 +160,6 @@ struct afc_problem_s {
   afc::DBuf<float2> up2, yp2;       // node vectors: u and y = f - AG u as pairs
   afc::DBuf<float2> abh2, abl2;     // node vectors: high and low parts of (A, B) = (u_max - u, u - u_min)
   afc::DBuf<float2> cp_up;          // Kup * N: clipped amount of each pair, at its lower row
-  afc::DBuf<unsigned int> fin_count;  // blocks of k_mcp_residual that have finished (last-block sum)
   afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
   // mixed-precision explicit stage: m_ij, d_ij, r_ij (Kup * N) and u, udot^L (node vectors) in single
   afc::DBuf<float> m32_up, d32_up, r32, uf, udf;

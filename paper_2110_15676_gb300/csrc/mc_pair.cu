@@ -23,8 +23,9 @@
 //                    of rows i and j);
 //  4. k_mcp_residual: res = y - sum_j c_ij on free rows (0 on Dirichlet rows), in
 //                    pairs, rounded to double once; block partials of res^2 (in pairs
-//                    while |res| < 2^60), summed by the last block when the caller
-//                    wants the norm.
+//                    while |res| < 2^60), summed by k_mcp_finalize when the caller
+//                    wants the norm (a separate one-block launch: a last-block sum
+//                    in the pass, with a fence and an atomic per block, was slower).
 // Accuracy: every value carries a relative error of at most 2^-48 and every product
 // and sum an error of that order relative to the magnitudes summed, so res agrees
 // with its FP64 evaluation to ~1e-14 of sum_j |AG_ij u_j| + sum_j |c_ij|, and the
@@ -219,48 +220,20 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf,
   }
 }
 
-// ||res||^2 from the block partials, by the block that finishes last (the blocks count
-// themselves on `count`, which that block resets).  The 256 threads take the roles of
-// the 1024 threads of k_finalize_sum (thread t those of t, t + 256, t + 512, t + 768:
-// the same strided sums, the same shuffle trees over the same lanes, the same warp
-// order), so the total is that kernel's bit for bit and the host-driven loop and the
-// graph (whose control kernel sums the partials the same way) stop alike.
-__device__ __forceinline__ void last_block_normsq(const double* part, unsigned int* count, double* out) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {   // the thread that stored the block's partial publishes it, then counts
-    __threadfence();
-    last = atomicAdd(count, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  if (threadIdx.x == 0) __threadfence();
-  __syncthreads();
-  const int n = gridDim.x;
-  double v[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) v[m] = warp_sum(strided_sum_1024(part, n, threadIdx.x + 256 * m));
-  __shared__ double sw[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) sw[w + 8 * m] = v[m];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const double t = warp_sum(sw[lane]);
-    if (lane == 0) {
-      *out = t;
-      *count = 0u;
-    }
-  }
+// ||res||^2 from the residual pass's block partials in k_finalize_sum's order (one
+// block of 1024 threads, so the graph's control kernel, which sums the same partials
+// the same way, stops alike), launched as the pass's dependent: it waits for the pass.
+__global__ void k_mcp_finalize(const double* __restrict__ part, int n, double* __restrict__ out) {
+  pdl_wait();
+  block_sum_to(strided_sum_1024(part, n, threadIdx.x), out);
 }
 
 template <int KT>
-__global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, int limiter,
+__global__ void __launch_bounds__(kBlock, 8) k_mcp_residual(int64_t N, Offsets of, int limiter,
                                                          const unsigned long long* __restrict__ clip,
                                                          const float2* __restrict__ c_up,
                                                          const float2* __restrict__ yp, const uint8_t* __restrict__ dir,
-                                                         double* __restrict__ res, double* __restrict__ part,
-                                                         unsigned int* __restrict__ count, double* __restrict__ normsq) {
+                                                         double* __restrict__ res, double* __restrict__ part) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool isdir = i < N && dir[i];
@@ -357,7 +330,6 @@ __global__ void __launch_bounds__(kBlock) k_mcp_residual(int64_t N, Offsets of, 
       part[blockIdx.x] = widen_exact(h) + widen_exact(l);
     }
   }
-  if (normsq) last_block_normsq(part, count, normsq);
 }
 
 // Pair copies of the stationary operator data (once, at assembly): AG, f and, per pair,
@@ -386,7 +358,7 @@ int mc_pair_setup(afc_problem_s* p) {
   int st;
   if ((st = p->AGp.alloc(p->K * N)) || (st = p->fp2.alloc(N, p->pad)) || (st = p->pairf_lo.alloc(3 * p->Kup * N)) ||
       (st = p->up2.alloc(N, p->pad)) || (st = p->abh2.alloc(N, p->pad)) || (st = p->abl2.alloc(N, p->pad)) ||
-      (st = p->yp2.alloc(N, p->pad)) || (st = p->fin_count.alloc(1)) ||
+      (st = p->yp2.alloc(N, p->pad)) ||
       (st = p->cp_up.alloc(p->Kup * N)))
     return st;
   AFC_LAUNCH(p, "k_mcp_setup", k_mcp_setup<<<grid_for(N), kBlock, 0, p->stream>>>(
@@ -443,8 +415,13 @@ int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res
     AFC_LAUNCH(p, "k_mcp_residual",
                e = launch_pass(pdl, k_mcp_residual<KT>, dim3((unsigned)g), dim3(kBlock), s, N, p->offs, limiter,
                                (const unsigned long long*)p->clip.p, (const float2*)p->cp_up.p, (const float2*)p->yp2.p,
-                               (const uint8_t*)p->dir.p, res, p->part.p, p->fin_count.p, normsq_slot));
-    if (e != cudaSuccess) st = cuda_fail(e, "launch k_mcp_residual");
+                               (const uint8_t*)p->dir.p, res, p->part.p));
+    if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_residual"); return; }
+    if (normsq_slot) {
+      AFC_LAUNCH(p, "k_mcp_finalize", e = launch_pass(pdl, k_mcp_finalize, dim3(1), dim3(1024), s,
+                                                      (const double*)p->part.p, (int)g, normsq_slot));
+      if (e != cudaSuccess) st = cuda_fail(e, "launch k_mcp_finalize");
+    }
   });
   if (st) return st;
   AFC_CUDA(cudaGetLastError());
