@@ -180,7 +180,6 @@ int dia_spmv(afc_problem_s* p, const double* A, const double* x, double* y) {
 // Solver workspace
 // ---------------------------------------------------------------------------
 constexpr int kMaxRestart = 32;   // GMRES(m), m <= 32: the Gram-Schmidt kernel keeps m dots in registers
-constexpr int kOrthQ = kMaxRestart;
 
 // device scalar slots
 enum : int {
@@ -277,8 +276,18 @@ __device__ __forceinline__ bool last_block_sums(double (&v)[NV], double* part, i
   const int n = gridDim.x;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
+    // thread t adds partials t, t + blockDim.x, ... in turn, the loads eight at a time
     double s = 0.0;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) s += __ldcg(part + q * pstride + b);
+    for (int b0 = threadIdx.x; b0 < n; b0 += 8 * blockDim.x) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + u * blockDim.x;
+        x[u] = b < n ? __ldcg(part + q * pstride + b) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += x[u];
+    }
     tot[q] = block_allsum(s);
   }
   if (threadIdx.x == 0) *counter = 0u;
@@ -510,9 +519,16 @@ __device__ __forceinline__ void grid_sums_end(double* part, int& buf, GridBar* b
   const double* pb = part + (size_t)buf * 2 * G;
   grid_wait(bar, old, wait_ns);
   if (w < NV) {
+    // lane l adds partials l, l + 32, ... in turn, the loads eight at a time (one round
+    // trip for up to 256 blocks)
     double t = 0.0;
-#pragma unroll 4
-    for (int b = lane; b < G; b += 32) t += __ldcg(pb + w * G + b);
+    for (int b0 = lane; b0 < G; b0 += 256) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = b0 + 32 * u < G ? __ldcg(pb + w * G + b0 + 32 * u) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += x[u];
+    }
     t = warp_sum(t);
     if (lane == 0) shtot[buf][w] = t;
   }
@@ -867,9 +883,17 @@ __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, i
   __shared__ double tot[QMAX + 1];
   {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // lane l adds partials l, l + 32, ... in turn, the loads eight at a time
+    const int n = gridDim.x;
     for (int q = wp; q < nq; q += nwarp) {
       double s = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + q * pstride + b);
+      for (int b0 = lane; b0 < n; b0 += 256) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = b0 + 32 * u < n ? __ldcg(part + q * pstride + b0 + 32 * u) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += x[u];
+      }
       s = warp_sum(s);
       if (lane == 0) tot[q] = s;
     }
@@ -918,17 +942,36 @@ __global__ void __launch_bounds__(256) k_gm_orth(int64_t N, double* sc, int k, i
   if (stop_test(fabs(g[k + 1]), sc) || sc[S_ITS] >= sc[S_MAXIT] || k + 1 == m || hk1 == 0.0) sc[S_CYCLE_DONE] = 1.0;
 }
 
-// Launch a Gram-Schmidt pass with the smallest register footprint that holds k + 1 dots.
+// Launch a Gram-Schmidt pass with the smallest register footprint that holds k + 1 dots,
+// on as many blocks as are resident at once (one wave), at most G.
+template <class T, int Q>
+int orth_grid(int G) {
+  static const int nb = [] {
+    int b = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gm_orth<T, Q>, kBlock, 0) != cudaSuccess) {
+      cudaGetLastError();
+      b = 0;
+    }
+    return b * nsm;
+  }();
+  return nb > 0 ? std::min(G, nb) : G;
+}
+
 template <class T>
 void orth_launch(afc_problem_s* p, int G, int64_t N, double* sc, int k, int m, int hslot, int outslot, T* w,
                  const T* V, size_t vs, double* part, int64_t pst, unsigned int* cnt) {
   cudaStream_t s = p->stream;
-  if (k + 1 <= 8)
-    AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, 8><<<G, kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt));
-  else if (k + 1 <= 16)
-    AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, 16><<<G, kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt));
-  else
-    AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, 32><<<G, kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt));
+#define AFC_ORTH(Q) AFC_LAUNCH(p, "k_gm_orth", k_gm_orth<T, Q><<<orth_grid<T, Q>(G), kBlock, 0, s>>>(N, sc, k, m, hslot, outslot, w, V, vs, part, pst, cnt))
+  if (k + 1 <= 4) AFC_ORTH(4);
+  else if (k + 1 <= 8) AFC_ORTH(8);
+  else if (k + 1 <= 12) AFC_ORTH(12);
+  else if (k + 1 <= 16) AFC_ORTH(16);
+  else if (k + 1 <= 20) AFC_ORTH(20);
+  else if (k + 1 <= 24) AFC_ORTH(24);
+  else AFC_ORTH(32);
+#undef AFC_ORTH
 }
 
 // back substitution H y = g for the k_used leading columns, then x += D^{-1} sum_q y_q V_q
@@ -943,12 +986,21 @@ __global__ void k_gm_update(int64_t N, const double* __restrict__ sc, T* __restr
   if (ku == 0) return;
   __shared__ double ys[kMaxRestart];
   __shared__ T yt[kMaxRestart];
+  // the leading ku x ku block of H and g, staged by the whole block (one round of loads
+  // instead of one dependent load per entry for the thread that solves)
+  __shared__ double hs[kMaxRestart * kMaxRestart];
+  __shared__ double gs[kMaxRestart];
+  for (int e = threadIdx.x; e < ku * ku; e += blockDim.x) {
+    const int q = e / ku, c = e - q * ku;
+    hs[q * kMaxRestart + c] = sc[S_HCOL + q * kMaxRestart + c];
+  }
+  for (int q = threadIdx.x; q < ku; q += blockDim.x) gs[q] = sc[S_G + q];
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double* H = sc + S_HCOL;
     for (int q = ku - 1; q >= 0; --q) {
-      double s = sc[S_G + q];
-      for (int c = q + 1; c < ku; ++c) s -= H[q * kMaxRestart + c] * ys[c];
-      ys[q] = s / H[q * kMaxRestart + q];
+      double s = gs[q];
+      for (int c = q + 1; c < ku; ++c) s -= hs[q * kMaxRestart + c] * ys[c];
+      ys[q] = s / hs[q * kMaxRestart + q];
     }
     for (int q = 0; q < ku; ++q) yt[q] = (T)ys[q];
   }
