@@ -157,7 +157,10 @@ __device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __
     const bool ok_j = !side_j || side_clear(d2h, ajh, xjh, ui.x, uj.x);
     if (ok_i && ok_j) return false;
   }
-  const float d2l = __ldcs(pfl + q), ail = __ldcs(pfl + KN + q), ajl = __ldcs(pfl + 2 * KN + q);
+  const float ail = __ldcs(pfl + KN + q), ajl = __ldcs(pfl + 2 * KN + q);
+  // low part of 2|d| = 2 max(0, k_ij, k_ji) (see k_mcp_edges): that of the larger of k_ij,
+  // k_ji, whose pairs are ordered as the doubles are
+  const float d2l = 2.f * (aih > ajh ? ail : ajh > aih ? ajl : fmaxf(ail, ajl));
   const float2 li = abl[i], lj = abl[j];
   const float xil = rpos ? li.x : li.y, xjl = rpos ? lj.y : lj.x;
   float Dh, Dl;   // |u_j - u_i|
@@ -206,7 +209,11 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf,
   const int64_t KN = (int64_t)Kup * N;
   // 2|d|, a_ij, a_ji (high parts), streamed past L2 so that the node arrays stay there;
   // no pass writes them, so they load before the wait for the rows pass
-  const float d2h = __ldcs(pf + q), aih = __ldcs(pf + KN + q), ajh = __ldcs(pf + 2 * KN + q);
+  const float aih = __ldcs(pf + KN + q), ajh = __ldcs(pf + 2 * KN + q);
+  // In the MC family D is the discrete upwinding of K: d_ij = -max(k_ij, 0, k_ji), so
+  // 2|d_ij| = 2 max(0, k_ij, k_ji) and its high part, twice the larger high part, is exact
+  // (rounding to float is monotone): the third plane of the pair data is not read.
+  const float d2h = 2.f * fmaxf(fmaxf(aih, 0.f), ajh);
   pdl_wait();
   const float2 ui = up[i], uj = up[j];
   const float2 bi = abh[i], bj = abh[j];
