@@ -156,7 +156,7 @@ struct afc_problem_s {
   afc::DBuf<float4> nodef;          // MC: (u, u_max - u, u - u_min) rounded to single
   // MC, mixed precision: the sweep in float pairs (mc_pair.cu)
   afc::DBuf<float2> AGp, fp2;       // K * N and N: AG and f as pairs
-  afc::DBuf<float> pairf_lo;        // 3 * Kup * N: low parts of 2|d_ij|, k_ij, k_ji
+  afc::DBuf<float2> pk_hi, pk_lo;   // Kup * N: (k_ij, k_ji) of each pair, high parts and low parts
   afc::DBuf<float2> up2, yp2;       // node vectors: u and y = f - AG u as pairs
   afc::DBuf<float2> abh2, abl2;     // node vectors: high and low parts of (A, B) = (u_max - u, u - u_min)
   afc::DBuf<float2> cp_up;          // Kup * N: clipped amount of each pair, at its lower row

@@ -141,9 +141,9 @@ __device__ __forceinline__ void side_value(float d2h, float d2l, float xh, float
 
 // One pair (i, j = i + o) of row i given its loaded data; returns true and the clipped
 // amount c_ij (c = -min(0, T_i, T_j) for r_ij > 0, min(0, T_i, T_j) for r_ij < 0) when
-// the pair is clipped.  The low parts of 2|d|, a_ij, a_ji are loaded only here, for the
-// pairs the pre-test cannot clear.
-__device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __restrict__ pfl,
+// the pair is clipped.  The low parts of a_ij, a_ji (and so of 2|d|) are loaded only here,
+// for the pairs the pre-test cannot clear.
+__device__ __forceinline__ bool pair_clip(int64_t q, const float2* __restrict__ pkl,
                                           const float2* __restrict__ abl, int64_t i, int64_t j, float d2h, float aih,
                                           float ajh, float2 ui, float2 uj, float2 bi, float2 bj, float2& c) {
   const bool side_i = aih > 0.f, side_j = ajh > 0.f;
@@ -157,7 +157,8 @@ __device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __
     const bool ok_j = !side_j || side_clear(d2h, ajh, xjh, ui.x, uj.x);
     if (ok_i && ok_j) return false;
   }
-  const float ail = __ldcs(pfl + KN + q), ajl = __ldcs(pfl + 2 * KN + q);
+  const float2 kl = __ldcs(pkl + q);
+  const float ail = kl.x, ajl = kl.y;
   // low part of 2|d| = 2 max(0, k_ij, k_ji) (see k_mcp_edges): that of the larger of k_ij,
   // k_ji, whose pairs are ordered as the doubles are
   const float d2l = 2.f * (aih > ajh ? ail : ajh > aih ? ajl : fmaxf(ail, ajl));
@@ -195,7 +196,7 @@ __device__ __forceinline__ bool pair_clip(int64_t q, int64_t KN, const float* __
 // Every load a pair needs for its pre-test is issued at once (one round trip to
 // memory); only the pairs the pre-test cannot clear load the low parts.
 template <int KT>
-__global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf, const float* __restrict__ pfl,
+__global__ void k_mcp_edges(int64_t N, Offsets of, const float2* __restrict__ pkh, const float2* __restrict__ pkl,
                             const float2* __restrict__ up, const float2* __restrict__ abh,
                             const float2* __restrict__ abl, float2* __restrict__ c_up,
                             unsigned long long* __restrict__ clip) {
@@ -206,19 +207,20 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float* __restrict__ pf,
   if (i >= N) return;
   const int64_t q = (int64_t)ku * N + i;
   const int64_t j = i + of.o[Kup + 1 + ku];
-  const int64_t KN = (int64_t)Kup * N;
-  // 2|d|, a_ij, a_ji (high parts), streamed past L2 so that the node arrays stay there;
-  // no pass writes them, so they load before the wait for the rows pass
-  const float aih = __ldcs(pf + KN + q), ajh = __ldcs(pf + 2 * KN + q);
+  // a_ij = k_ij, a_ji = k_ji (high parts, one 8-byte load), streamed past L2 so that the
+  // node arrays stay there; no pass writes them, so they load before the wait for the rows
+  // pass
+  const float2 kh = __ldcs(pkh + q);
+  const float aih = kh.x, ajh = kh.y;
   // In the MC family D is the discrete upwinding of K: d_ij = -max(k_ij, 0, k_ji), so
   // 2|d_ij| = 2 max(0, k_ij, k_ji) and its high part, twice the larger high part, is exact
-  // (rounding to float is monotone): the third plane of the pair data is not read.
+  // (rounding to float is monotone), and no copy of it is read.
   const float d2h = 2.f * fmaxf(fmaxf(aih, 0.f), ajh);
   pdl_wait();
   const float2 ui = up[i], uj = up[j];
   const float2 bi = abh[i], bj = abh[j];
   float2 c;
-  if (pair_clip(q, KN, pfl, abl, i, j, d2h, aih, ajh, ui, uj, bi, bj, c)) {
+  if (pair_clip(q, pkl, abl, i, j, d2h, aih, ajh, ui, uj, bi, bj, c)) {
     c_up[q] = c;
     // the pair's bit at both ends: offset index Kup + 1 + ku at row i, Kup - 1 - ku
     // (the offset -o back to i) at row j
@@ -342,21 +344,20 @@ __global__ void __launch_bounds__(kBlock, KT == 27 ? 1 : 8) k_mcp_residual(int64
 }
 
 // Pair copies of the stationary operator data (once, at assembly): AG, f and, per pair,
-// the low parts of 2|d_ij|, k_ij, k_ji (their high parts are mc.cu's single copies).
+// (k_ij, k_ji) as high parts and as low parts.
 __global__ void k_mcp_setup(int64_t N, Offsets of, const double* __restrict__ AG, const double* __restrict__ f,
-                            const double* __restrict__ d2, const double* __restrict__ kij,
-                            const double* __restrict__ kji, float2* __restrict__ AGp, float2* __restrict__ fp,
-                            float* __restrict__ pfl) {
+                            const double* __restrict__ kij, const double* __restrict__ kji,
+                            float2* __restrict__ AGp, float2* __restrict__ fp, float2* __restrict__ pkh,
+                            float2* __restrict__ pkl) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int k = 0; k < of.K; ++k) AGp[(int64_t)k * N + i] = split_pair(AG[(int64_t)k * N + i]);
   fp[i] = split_pair(f[i]);
-  const int64_t KN = (int64_t)of.Kup * N;
   for (int ku = 0; ku < of.Kup; ++ku) {
     const int64_t q = (int64_t)ku * N + i;
-    pfl[q] = split_pair(d2[q]).y;
-    pfl[KN + q] = split_pair(kij[q]).y;
-    pfl[2 * KN + q] = split_pair(kji[q]).y;
+    const float2 a = split_pair(kij[q]), b = split_pair(kji[q]);
+    pkh[q] = make_float2(a.x, b.x);
+    pkl[q] = make_float2(a.y, b.y);
   }
 }
 
@@ -365,14 +366,15 @@ __global__ void k_mcp_setup(int64_t N, Offsets of, const double* __restrict__ AG
 int mc_pair_setup(afc_problem_s* p) {
   const int64_t N = p->N;
   int st;
-  if ((st = p->AGp.alloc(p->K * N)) || (st = p->fp2.alloc(N, p->pad)) || (st = p->pairf_lo.alloc(3 * p->Kup * N)) ||
+  if ((st = p->AGp.alloc(p->K * N)) || (st = p->fp2.alloc(N, p->pad)) || (st = p->pk_hi.alloc(p->Kup * N)) ||
+      (st = p->pk_lo.alloc(p->Kup * N)) ||
       (st = p->up2.alloc(N, p->pad)) || (st = p->abh2.alloc(N, p->pad)) || (st = p->abl2.alloc(N, p->pad)) ||
       (st = p->yp2.alloc(N, p->pad)) ||
       (st = p->cp_up.alloc(p->Kup * N)))
     return st;
   AFC_LAUNCH(p, "k_mcp_setup", k_mcp_setup<<<grid_for(N), kBlock, 0, p->stream>>>(
-                                   N, p->offs, p->AG.p, p->f.p, p->d2_up.p, p->kij_up.p, p->kji_up.p, p->AGp.p,
-                                   p->fp2.p, p->pairf_lo.p));
+                                   N, p->offs, p->AG.p, p->f.p, p->kij_up.p, p->kji_up.p, p->AGp.p, p->fp2.p,
+                                   p->pk_hi.p, p->pk_lo.p));
   AFC_CUDA(cudaGetLastError());
   return AFC_OK;
 }
@@ -417,7 +419,7 @@ int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res
     if (limiter == AFC_LIM_MC) {
       AFC_LAUNCH(p, "k_mcp_edges",
                  e = launch_pass(pdl, k_mcp_edges<KT>, dim3((unsigned)grid_for(N, 32)), dim3(32, p->Kup), s, N, p->offs,
-                                 (const float*)p->pairf.p, (const float*)p->pairf_lo.p, (const float2*)p->up2.p,
+                                 (const float2*)p->pk_hi.p, (const float2*)p->pk_lo.p, (const float2*)p->up2.p,
                                  (const float2*)p->abh2.p, (const float2*)p->abl2.p, p->cp_up.p, p->clip.p));
       if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_edges"); return; }
     }
