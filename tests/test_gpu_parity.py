@@ -521,6 +521,30 @@ def test_linear_solves(afc, system, ksp, precision):
         assert relerr(x, x_ref) < 1e-10
 
 
+@pytest.mark.parametrize("restart", [4, 13, 25, 32])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gmres_restart_lengths(afc, restart, precision):
+    """GMRES(m) for restart lengths whose Arnoldi steps use every register class of the
+    Gram-Schmidt pass (k + 1 up to 4, 8, 12, 16, 20, 24, 32), against a direct solve."""
+    wl = random_workload("q1", (11, 9, 8), seed=3)
+    o, g = pair_from_workload(wl, "mc", precision=precision)
+    B = O.stationary_system_matrix(o)
+    rhs = np.random.default_rng(restart).normal(size=o.mesh.n_nodes)
+    x_ref = spla.spsolve(B.tocsc(), rhs)
+    mixed = precision == "mixed"
+    opts = afc.default_opts(ksp=afc.AFC_KSP_GMRES, ksp_atol=0.0 if mixed else 1e-12,
+                            ksp_rtol=1e-6 if mixed else 0.0, ksp_maxit=5000, gmres_restart=restart,
+                            precision=afc.AFC_MIXED if mixed else afc.AFC_FP64)
+    x, its, res = g.linear_solve(0, rhs, opts, 0.0)
+    assert its > 0
+    true_res = np.linalg.norm(rhs - B @ x)
+    if mixed:
+        assert true_res < 1e-5 * np.linalg.norm(rhs)
+    else:
+        assert true_res < 2e-12
+        assert relerr(x, x_ref) < 1e-10
+
+
 def test_low_order_apply(afc):
     wl = random_workload("p1", (13, 11, 7), seed=8)
     o, g = pair_from_workload(wl)
