@@ -463,6 +463,14 @@ int afc_profile_read(afc_problem p, int cap, char* names, double* total_ms, int6
  * device memory. */
 int afc_selftest_grid_wait(int device, double limit_ms, int* observed, double* waited_ms);
 
+/* Self-test of the float-pair arithmetic of the mixed MC sweep (the split of a double
+ * into the pair hi = RN(x), lo = RN(x - hi) on the integer pipe, and the exact widening
+ * of a float to double): on `device`, for the n doubles of the host array x, writes
+ * hi[i], lo[i] and hi_widened[i] = hi[i] as a double (host arrays of n values, owned by
+ * the caller).  0 <= n <= 2^26.  Returns AFC_OK, AFC_E_INVALID for a bad n or a NULL
+ * array, AFC_E_CUDA on a CUDA error.  Allocates and frees 24 n bytes of device memory. */
+int afc_selftest_split(int device, const double* x, int64_t n, float* hi, float* lo, double* hi_widened);
+
 /* Limit of the bounded waits at the grid barriers of this problem's persistent
  * BiCGStab launches (default 4000 ms, the largest allowed; 0 <= limit_ms <= 4000).
  * A wait that reaches it records the error and every later barrier of the launch

@@ -140,6 +140,7 @@ _SIGS = {
     "afc_serve_get_info": (C.c_int, [_P, C.POINTER(afc_serve_info)]),
     "afc_serve_destroy": (C.c_int, [_P]),
     "afc_selftest_grid_wait": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_int), _D]),
+    "afc_selftest_split": (C.c_int, [C.c_int, _D, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_float), _D]),
     "afc_set_grid_wait_limit": (C.c_int, [_P, C.c_double]),
     "afc_status_str": (C.c_char_p, [C.c_int]),
     "afc_last_error": (C.c_char_p, []),
@@ -197,6 +198,20 @@ def _f64(a, n=None) -> np.ndarray:
     if n is not None and a.size != n:
         raise ValueError(f"expected {n} values, got {a.size}")
     return a
+
+
+def selftest_split(x, device: int = 0):
+    """Run afc_selftest_split: the device's float pairs (hi, lo) of the doubles x and hi
+    widened back to double."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    n = a.size
+    hi = np.zeros(n, np.float32)
+    lo = np.zeros(n, np.float32)
+    back = np.zeros(n, np.float64)
+    fp = C.POINTER(C.c_float)
+    _check(_lib.afc_selftest_split(int(device), _dp(a), n, hi.ctypes.data_as(fp), lo.ctypes.data_as(fp), _dp(back)),
+           "afc_selftest_split")
+    return hi, lo, back
 
 
 def selftest_grid_wait(limit_ms: float = 50.0, device: int = 0) -> tuple[int, float]:

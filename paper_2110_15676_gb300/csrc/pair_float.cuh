@@ -63,7 +63,7 @@ __device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl,
 // Doubles of magnitude 2^127 or more, Inf and NaN, beyond the range of float pairs:
 // kept out of line so that its FP64 instructions issue only for the warps that need
 // them.
-__device__ __noinline__ float2 split_pair_fp64(double x) {
+static __device__ __noinline__ float2 split_pair_fp64(double x) {
   const float h = __double2float_rn(x);
   return make_float2(h, __double2float_rn(x - (double)h));
 }

@@ -6,6 +6,8 @@
 #include <chrono>
 
 #include "grid_sync.cuh"
+#include "kernels_common.cuh"
+#include "pair_float.cuh"
 
 namespace afc {
 namespace {
@@ -18,6 +20,17 @@ __global__ void k_grid_wait_selftest(GridBar* gb, unsigned long long limit_ns) {
 
 __global__ void k_selftest_touch(int* x) {
   if (threadIdx.x == 0) *x = 7;
+}
+
+// The float-pair split and the exact widening of the mixed MC sweep, element by element.
+__global__ void k_selftest_split(int64_t n, const double* __restrict__ x, float* __restrict__ hi,
+                                 float* __restrict__ lo, double* __restrict__ back) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 p = split_pair(x[i]);
+  hi[i] = p.x;
+  lo[i] = p.y;
+  back[i] = widen_exact(p.x);
 }
 
 }  // namespace
@@ -67,5 +80,35 @@ extern "C" int afc_selftest_grid_wait(int device, double limit_ms, int* observed
     }
   } while (false);
   cudaFree(gb);
+  return st;
+}
+
+extern "C" int afc_selftest_split(int device, const double* x, int64_t n, float* hi, float* lo, double* hi_widened) {
+  if (n < 0 || (n > 0 && (!x || !hi || !lo || !hi_widened)) || n > ((int64_t)1 << 26)) {
+    set_error("afc_selftest_split: need 0 <= n <= 2^26 and host arrays of n values");
+    return AFC_E_INVALID;
+  }
+  if (n == 0) return AFC_OK;
+  AFC_CUDA(cudaSetDevice(device));
+  char* buf = nullptr;
+  const size_t bx = (size_t)n * sizeof(double), bf = (size_t)n * sizeof(float);
+  AFC_CUDA(cudaMalloc((void**)&buf, 2 * bx + 2 * bf));
+  double* dx = reinterpret_cast<double*>(buf);
+  double* db = reinterpret_cast<double*>(buf + bx);
+  float* dh = reinterpret_cast<float*>(buf + 2 * bx);
+  float* dl = reinterpret_cast<float*>(buf + 2 * bx + bf);
+  int st = AFC_OK;
+  cudaError_t e;
+  if ((e = cudaMemcpy(dx, x, bx, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    st = cuda_fail(e, "cudaMemcpy");
+  } else {
+    k_selftest_split<<<(unsigned)((n + 255) / 256), 256>>>(n, dx, dh, dl, db);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess ||
+        (e = cudaMemcpy(hi, dh, bf, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(lo, dl, bf, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(hi_widened, db, bx, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      st = cuda_fail(e, "k_selftest_split");
+  }
+  cudaFree(buf);
   return st;
 }
