@@ -6,8 +6,10 @@
 //   res = f - AG u - sum_j c_ij,   AG = K + eps S + c M_L,
 // and c_ij = max(0, -T_i, -T_j) (r_ij > 0) or min(0, T_i, T_j) (r_ij < 0) with
 // T = 2|d_ij| X - a |u_j - u_i|, X the room of the side in its bounds.  The matrix AG,
-// f, 2|d_ij|, k_ij and k_ji are stored as float pairs (8 bytes per value, as many as
-// a double), and the state is split into pairs once per sweep, so that the sweep
+// f, k_ij and k_ji are stored as float pairs (8 bytes per value, as many as a double;
+// (k_ij, k_ji) interleaved per pair, high parts and low parts apart; 2|d_ij| =
+// 2 max(0, k_ij, k_ji) is formed from them), and the state is split into pairs once
+// per sweep, so that the sweep
 // issues no FP64 instruction per matrix entry or per pair: on GB300 one FP64 warp
 // instruction per pair of the P1 129^3 grid alone costs ~23 us, which is what
 // bounded the FP64 form.
