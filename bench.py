@@ -435,7 +435,7 @@ def batched(afc, W, torch, stream, steps=50, count=256, seed=4, shape=None, solo
 
 
 def serving(afc, W, rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), count=48, seed=5, stat_maxit=1000,
-            serial_rates=(10.0, 500.0)):
+            serial_rates=(10.0, 500.0), workers=8, builders=4):
     """Poisson streams of stationary and transient CDR requests (P1 or Q1, nodes per
     side uniform in [17, 97], eps log-uniform [1e-8, 1e-4], c uniform [0, 1]):
     the batched server with mixed precision against the serial server with FP64
@@ -471,7 +471,7 @@ def serving(afc, W, rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), count=48, see
         for name, (mode, rq) in arms.items():
             if name == "serial_fp64" and rate not in serial_rates:
                 continue
-            with afc.Server(mode=mode, stationary_workers=8, max_chunk=10, builders=4) as srv:
+            with afc.Server(mode=mode, stationary_workers=workers, max_chunk=10, builders=builders) as srv:
                 t0 = time.perf_counter()
                 ids = []
                 for t_arr, r in zip(arr, rq):
@@ -523,8 +523,9 @@ def serving(afc, W, rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), count=48, see
                         f"n in [17, 97], "
                         f"eps log-uniform [1e-8, 1e-4], c in [0, 1]; Poisson arrivals",
             "rates": rows, "mixed_max_rel_diff_vs_fp64": diff,
-            "arms": "batched_mixed: 4 builders, continuous batching of transient requests, 8 concurrent stationary "
-                    "solves, FP32 inner solves / fluxes, float-pair MC residual; serial_fp64: one request at a time, "
+            "arms": f"batched_mixed: {builders} builders, continuous batching of transient requests, {workers} "
+                    "concurrent stationary solves, FP32 inner solves / fluxes, float-pair MC residual; serial_fp64: "
+                    "one request at a time, "
                     f"FP64, at rates {list(serial_rates)}"}
 
 
@@ -572,7 +573,8 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     if args.only_serving:
-        print(json.dumps({"serving": serving(afc, W, count=args.serving_count)}))
+        print(json.dumps({"serving": serving(afc, W, count=args.serving_count, workers=args.serving_workers,
+                                             builders=args.serving_builders)}))
         return
     if args.only_batched:
         shape = None
@@ -677,7 +679,7 @@ def run_ours(args, ws, rank, local):
 
     srv = None
     if not args.no_serving and args.steps > 0:
-        srv = serving(afc, W, count=args.serving_count)
+        srv = serving(afc, W, count=args.serving_count, workers=args.serving_workers, builders=args.serving_builders)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -860,6 +862,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--only-serving", action="store_true", help="time only the request-server streams")
     ap.add_argument("--serving-count", type=int, default=48)
+    ap.add_argument("--serving-workers", type=int, default=8, help="concurrent stationary solves of the server")
+    ap.add_argument("--serving-builders", type=int, default=4, help="problem-building threads of the server")
     ap.add_argument("--cpu-rounds", type=int, default=2, help="timed rounds of the CPU baseline")
     args = ap.parse_args()
     ws, rank, local = _dist()
