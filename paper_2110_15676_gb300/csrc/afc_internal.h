@@ -233,6 +233,7 @@ struct KrylovEpilogue {
   const double* uo = nullptr;
   double* a = nullptr;
   double* s = nullptr;
+  double* fp_sc = nullptr;   // graph form: the fixed-point scalars, where the solve counts itself
 };
 // *epi_done (if given) tells whether the solve applied *epi; when it did not, the
 // caller applies the update itself.

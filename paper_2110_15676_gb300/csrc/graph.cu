@@ -19,14 +19,6 @@ namespace afc {
 
 namespace {
 
-// fixed-point scalar slots (problem scalars p->scal)
-enum : int {
-  F_NORMSQ = 0, F_CORR = 1, F_INNER = 2, F_RES0 = 3, F_RESF = 4, F_STATUS = 5, F_THRESH = 6, F_FIXED = 7,
-  F_MAXIT = 8, F_KBODY = 9, F_REVAL = 10, F_TIMEOUT = 11
-};
-// F_STATUS: 0 running, 1 converged / fixed count reached, 2 non-finite or a solver that
-// could not finish, 3 iteration limit; F_TIMEOUT: 1 after a grid barrier of the
-// persistent BiCGStab gave up waiting (F_STATUS is then 2)
 
 __global__ void k_fp_init(double* sc, double thresh, int fixed, int maxit) {
   if (threadIdx.x != 0) return;
@@ -253,15 +245,21 @@ int build_fixed_point(afc_problem_s* p, const afc_opts* o, int system, Pro prolo
     std::vector<cudaGraphNode_t> sf;
     const int64_t l0 = p->launches;
     bool applied = false;   // the persistent BiCGStab applies the update itself
-    if ((st = krylov_graph(p, system, o, p->res.p, p->delta.p, cs, sbody, sf, epi, &applied))) break;
+    // ... and then also counts the correction in the fixed-point scalars (no after-solve node)
+    KrylovEpilogue epc;
+    if (epi) {
+      epc = *epi;
+      epc.fp_sc = p->scal.p;
+    }
+    if ((st = krylov_graph(p, system, o, p->res.p, p->delta.p, cs, sbody, sf, epi ? &epc : nullptr, &applied)))
+      break;
     const int64_t lk = p->launches - l0;
     const int64_t body_k = o->ksp == AFC_KSP_GMRES ? 3 + 5 * (int64_t)o->gmres_restart : 5;
     auto r3 = count([&]() -> int {
       return capture_into(p, cs, sbody, sf, [&]() -> int {
-        if (!applied) {
-          int s = update();
-          if (s) return s;
-        }
+        if (applied) return AFC_OK;   // the fused solve updated u and counted the correction
+        int s = update();
+        if (s) return s;
         AFC_LAUNCH(p, "k_fp_after_solve",
                    k_fp_after_solve<<<1, 32, 0, p->stream>>>(p->scal.p, krylov_scalars(p),
                                                              o->ksp == AFC_KSP_GMRES ? 1 : 0, krylov_cycles_slot()));

@@ -64,6 +64,15 @@ constexpr int kKrylovItsSlot = 7;
 constexpr int kKrylovDoneSlot = 8;
 // 1 after a grid barrier of the persistent BiCGStab launch gave up waiting
 constexpr int kKrylovBarrierErrSlot = 19;
+
+// fixed-point scalar slots (problem scalars p->scal)
+enum : int {
+  F_NORMSQ = 0, F_CORR = 1, F_INNER = 2, F_RES0 = 3, F_RESF = 4, F_STATUS = 5, F_THRESH = 6, F_FIXED = 7,
+  F_MAXIT = 8, F_KBODY = 9, F_REVAL = 10, F_TIMEOUT = 11
+};
+// F_STATUS: 0 running, 1 converged / fixed count reached, 2 non-finite or a solver that
+// could not finish, 3 iteration limit; F_TIMEOUT: 1 after a grid barrier of the
+// persistent BiCGStab gave up waiting (F_STATUS is then 2)
 int krylov_cycles_slot();
 // Clear the grid barrier state of the persistent BiCGStab after a timeout (its
 // counter is left inconsistent when blocks skip barriers); synchronises the stream.

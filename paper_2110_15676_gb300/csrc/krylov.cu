@@ -697,6 +697,14 @@ __global__ void __launch_bounds__(kFusedBlock, 1024 / kFusedBlock) k_bicg_fused(
     sc[S_RHO] = rho;
     sc[S_DONE] = *berr ? 2.0 : (double)done;
     sc[S_BERR] = *berr ? 1.0 : 0.0;
+    if (ep.fp_sc) {   // the fixed-point loop's count of this correction (the after-solve node's work)
+      double* f = ep.fp_sc;
+      f[F_CORR] += 1.0;
+      f[F_INNER] += (double)its;
+      f[F_KBODY] += (double)its;
+      if (*berr || done == 2) f[F_STATUS] = 2.0;
+      if (*berr) f[F_TIMEOUT] = 1.0;
+    }
   }
 }
 
