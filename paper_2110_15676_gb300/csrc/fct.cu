@@ -124,8 +124,11 @@ __global__ void k_cn_edges(int64_t N, Offsets of, const double* __restrict__ mdt
   if (i >= N) return;
   const int64_t q = (int64_t)ku * N + i;
   const int64_t j = i + of.o[Kup + 1 + ku];
-  const double lim = d_up[q] * (s[j] - s[i]);
-  double r = fma(mdt_up[q], a[i] - a[j], half_exact(lim));
+  pdl_trigger();
+  const double dq = d_up[q], mq = mdt_up[q];   // no pass of the step writes them
+  pdl_wait();
+  const double lim = dq * (s[j] - s[i]);
+  double r = fma(mq, a[i] - a[j], half_exact(lim));
   if (prelimit) r = minmod(r, lim);
   r_up[q] = r;
 }
@@ -138,10 +141,16 @@ __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __
                              const uint8_t* __restrict__ dir, double dt, double* __restrict__ Rp,
                              double* __restrict__ Rm) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (dir[i]) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
+  // the mask, the Dirichlet flag and m Q+/- (formed once per step) before the wait for
+  // the fluxes of the edge pass
+  const bool isdir = dir[i];
   const unsigned long long mk = mask[i];
+  const double qp = mQp[i], qm = mQm[i];
+  pdl_wait();
+  if (isdir) { Rp[i] = 1.0; Rm[i] = 1.0; return; }
   constexpr int KA = KT > 0 ? KT : kMaxOffsets;
   SignedFixedSums acc;
 #pragma unroll
@@ -151,8 +160,8 @@ __global__ void k_cn_factors(int64_t N, Offsets of, const unsigned long long* __
   }
   double Pp, Pm;
   acc.result(Pp, Pm);
-  Rp[i] = zalesak_factor(mQp[i], dt * Pp);
-  Rm[i] = zalesak_factor(mQm[i], dt * Pm);
+  Rp[i] = zalesak_factor(qp, dt * Pp);
+  Rm[i] = zalesak_factor(qm, dt * Pm);
 }
 
 // Zalesak step 4, F*, and the nonlinear residual of Eq. CNZal:
@@ -166,15 +175,22 @@ __global__ void __launch_bounds__(256, 4) k_cn_residual(int64_t N, Offsets of, i
                               const double* __restrict__ mLdt, const uint8_t* __restrict__ dir,
                               double* __restrict__ res, double* __restrict__ Fout, double* __restrict__ part) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double r2 = 0.0;
+  // y = AA u from the matrix and the state, before the wait for the factors pass: no pass
+  // of the limiter writes them (u is the solver's, complete before the edge pass started)
+  const bool act = i < N && !dir[i];
+  double y = 0.0;
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], un[i + of.o[k]], y);
+  }
+  pdl_wait();
   if (i < N) {
     double rv = 0.0, F = 0.0;
-    if (!dir[i]) {
+    if (act) {
       const unsigned long long mk = mask[i];
-      double y = 0.0;
-    #pragma unroll
-  for (int k = 0; k < K; ++k) y = fma(AA[k * N + i], un[i + of.o[k]], y);
       if (limiter != AFC_LIM_NONE) {
         const double rpi = Rp[i], rmi = Rm[i];
       #pragma unroll
@@ -425,14 +441,20 @@ int cn_limited_residual(afc_problem_s* p, const double* u_new, double dt, int li
     if (limiter != AFC_LIM_NONE)
       AFC_LAUNCH(p, "k_cn_edges", k_cn_edges<KT><<<grid_for(N, 32), dim3(32, p->Kup), 0, s>>>(N, p->offs, p->mdt_up.p, p->d_up.p, p->cn_a.p,
                                                                        p->cn_s.p, prelimit, p->r_up.p));
+    // programmatic dependent launch down the limiter passes (the edge pass follows the
+    // solver with a plain dependency)
     if (limiter == AFC_LIM_ZALESAK)
-      AFC_LAUNCH(p, "k_cn_factors", k_cn_factors<KT><<<g, kBlock, 0, s>>>(N, p->offs, p->mask.p, p->r_up.p, p->Qp.p,
-                                                                           p->Qm.p, p->dir.p, dt, p->Rp.p,
-                                                                           p->Rm.p));
+      AFC_LAUNCH(p, "k_cn_factors", launch_pass(limiter != AFC_LIM_NONE, k_cn_factors<KT>, dim3((unsigned)g),
+                                                dim3(kBlock), s, N, p->offs, (const unsigned long long*)p->mask.p,
+                                                (const double*)p->r_up.p, (const double*)p->Qp.p,
+                                                (const double*)p->Qm.p, (const uint8_t*)p->dir.p, dt, p->Rp.p,
+                                                p->Rm.p));
     AFC_LAUNCH(p, "k_cn_residual",
-               k_cn_residual<KT><<<g, kBlock, 0, s>>>(N, p->offs, limiter, p->mask.p, p->r_up.p, p->AA.p, u_new,
-                                                      p->Rp.p, p->Rm.p, p->b0.p, p->mLdt.p, p->dir.p, res, p->Fs.p,
-                                                      p->part.p));
+               launch_pass(limiter != AFC_LIM_NONE, k_cn_residual<KT>, dim3((unsigned)g), dim3(kBlock), s, N,
+                           p->offs, limiter, (const unsigned long long*)p->mask.p, (const double*)p->r_up.p,
+                           (const double*)p->AA.p, u_new, (const double*)p->Rp.p, (const double*)p->Rm.p,
+                           (const double*)p->b0.p, (const double*)p->mLdt.p, (const uint8_t*)p->dir.p, res, p->Fs.p,
+                           p->part.p));
   });
   if (normsq_slot) finalize_sum(p, p->part.p, (int)g, normsq_slot);
   AFC_CUDA(cudaGetLastError());

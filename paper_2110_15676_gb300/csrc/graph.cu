@@ -38,6 +38,7 @@ __global__ void k_fp_init(double* sc, double thresh, int fixed, int maxit) {
 // (the order of finalize_sum) before the decision, so the sum needs no launch of its own.
 __global__ void k_fp_control(double* sc, const double* __restrict__ part, int npart,
                              cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_solve) {
+  pdl_wait();   // the residual pass's partials (a no-op when launched without the attribute)
   block_sum_to(strided_sum_1024(part, npart, threadIdx.x), sc + F_NORMSQ);   // one block of 1024
   if (threadIdx.x != 0) return;
   const double R = sqrt(sc[F_NORMSQ]);
@@ -230,8 +231,12 @@ int build_fixed_point(afc_problem_s* p, const afc_opts* o, int system, Pro prolo
       return capture_into(p, cs, body, {}, [&]() -> int {
         int s = residual();
         if (s) return s;
-        AFC_LAUNCH(p, "k_fp_control", k_fp_control<<<1, 1024, 0, p->stream>>>(p->scal.p, p->part.p,
-                                                                               (int)grid_for(p->N), h_loop, h_solve));
+        // programmatic dependency on the Zalesak CN residual pass, which ends the body's residual
+        // (the other residuals end with other work and keep a plain one)
+        const bool pdl = system == 1 && o->limiter == AFC_LIM_ZALESAK;
+        AFC_LAUNCH(p, "k_fp_control", launch_pass(pdl, k_fp_control, dim3(1), dim3(1024), p->stream,
+                                                  p->scal.p, (const double*)p->part.p, (int)grid_for(p->N), h_loop,
+                                                  h_solve));
         AFC_CUDA(cudaGetLastError());
         return AFC_OK;
       }, bf);

@@ -320,6 +320,29 @@ inline void with_K(int K, F&& f) {
   else f(std::integral_constant<int, 0>{});
 }
 
+// Programmatic dependent launch between consecutive passes: a pass lets the next one
+// launch as soon as all of its blocks run (griddepcontrol.launch_dependents), and the
+// next pass issues the loads of data no earlier pass writes before it waits for its
+// predecessor's results (griddepcontrol.wait), so those loads overlap the predecessor's
+// last wave.  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch kernel k with programmatic dependent launch on `pdl`.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pass(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // out[0] = sum of part[0..n) in a fixed order (one block).
 void finalize_sum(afc_problem_s* p, const double* part, int n, double* out);
 

@@ -40,15 +40,6 @@ namespace afc {
 
 namespace {
 
-// Programmatic dependent launch between the passes of a sweep: a pass lets the next
-// one launch as soon as all of its blocks run (griddepcontrol.launch_dependents), and
-// the next pass issues the loads of data no earlier pass writes (the matrix, the pair
-// coefficients, the Dirichlet mask) before it waits for its predecessor's results
-// (griddepcontrol.wait), so those loads overlap the predecessor's last wave.  Launched
-// without the attribute, both are no-ops.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 __global__ void k_mcp_split(int64_t N, const double* __restrict__ u, float2* __restrict__ up) {
   pdl_trigger();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -381,22 +372,6 @@ int mc_pair_setup(afc_problem_s* p) {
   return AFC_OK;
 }
 
-namespace {
-// A pass of the sweep, launched with programmatic dependent launch on `pdl`.
-template <class... KArgs, class... Args>
-cudaError_t launch_pass(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = g;
-  cfg.blockDim = b;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k, args...);
-}
-}  // namespace
 
 int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res, double* normsq_slot) {
   const int64_t N = p->N;
