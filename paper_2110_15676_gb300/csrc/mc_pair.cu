@@ -32,6 +32,8 @@
 // and sum an error of that order relative to the magnitudes summed, so res agrees
 // with its FP64 evaluation to ~1e-14 of sum_j |AG_ij u_j| + sum_j |c_ij|, and the
 // bounds are exact up to pairs that tie within 2^-48.
+#include <type_traits>
+
 #include "afc_internal.h"
 #include "kernels_common.cuh"
 #include "pair_float.cuh"
@@ -40,6 +42,18 @@ namespace afc {
 
 namespace {
 
+// Word of the per-row presence and clip masks (bit k: offset k): 32 bits when the
+// offsets are known at compile time to number at most 32 (P1: 15, Q1: 27), which
+// halves the masks' traffic and the edge pass's atomics; 64 bits otherwise.
+template <int KT>
+using MaskWord = std::conditional_t<(KT > 0 && KT <= 32), unsigned, unsigned long long>;
+
+// The presence masks in 32 bits (once, at assembly).
+__global__ void k_mcp_mask32(int64_t N, const unsigned long long* __restrict__ mask, unsigned* __restrict__ m32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) m32[i] = (unsigned)mask[i];
+}
+
 __global__ void k_mcp_split(int64_t N, const double* __restrict__ u, float2* __restrict__ up) {
   pdl_trigger();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -47,18 +61,18 @@ __global__ void k_mcp_split(int64_t N, const double* __restrict__ u, float2* __r
 }
 
 template <int KT>
-__global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, const unsigned long long* __restrict__ mask,
+__global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, const MaskWord<KT>* __restrict__ mask,
                                                      const float2* __restrict__ up, const float2* __restrict__ AGp,
                                                      const float2* __restrict__ fp, float2* __restrict__ yp,
                                                      float2* __restrict__ abh, float2* __restrict__ abl,
-                                                     unsigned long long* __restrict__ clip) {
+                                                     MaskWord<KT>* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K;
   pdl_trigger();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   // the row's matrix entries, mask and source first (no pass writes them), then, once
   // the split is done, its states: all loads of the row in flight together
-  const unsigned long long mk = __ldcs(mask + i);
+  const MaskWord<KT> mk = __ldcs(mask + i);
   const float2 f = __ldcs(fp + i);
   constexpr int KL = KT > 0 ? KT : 1;
   float2 vv[KL], aa[KL];
@@ -83,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, cons
     two_sum(sh, -ph, s, e);
     sh = s;
     sl = __fadd_rn(sl, __fsub_rn(e, pl));
-    if ((mk >> k) & 1ull) {
+    if ((mk >> k) & 1u) {
       if (pair_gt(v.x, v.y, mxh, mxl)) {
         mxh = v.x;
         mxl = v.y;
@@ -104,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_mcp_rows(int64_t N, Offsets of, cons
   if (Bh < 0.f) Bh = Bl = 0.f;
   abh[i] = make_float2(Ah, Bh);
   abl[i] = make_float2(Al, Bl);
-  clip[i] = 0ull;
+  clip[i] = 0;
 }
 
 // The pre-test of mc.cu (k_mc_edges), on the high parts: T = 2|d| X - a |D| is
@@ -192,7 +206,7 @@ template <int KT>
 __global__ void k_mcp_edges(int64_t N, Offsets of, const float2* __restrict__ pkh, const float2* __restrict__ pkl,
                             const float2* __restrict__ up, const float2* __restrict__ abh,
                             const float2* __restrict__ abl, float2* __restrict__ c_up,
-                            unsigned long long* __restrict__ clip) {
+                            MaskWord<KT>* __restrict__ clip) {
   const int K = KT > 0 ? KT : of.K, Kup = K / 2;
   pdl_trigger();
   const int ku = threadIdx.y;
@@ -217,8 +231,8 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float2* __restrict__ pk
     c_up[q] = c;
     // the pair's bit at both ends: offset index Kup + 1 + ku at row i, Kup - 1 - ku
     // (the offset -o back to i) at row j
-    atomicOr(clip + i, 1ull << (Kup + 1 + ku));
-    atomicOr(clip + j, 1ull << (Kup - 1 - ku));
+    atomicOr(clip + i, (MaskWord<KT>)1 << (Kup + 1 + ku));
+    atomicOr(clip + j, (MaskWord<KT>)1 << (Kup - 1 - ku));
   }
 }
 
@@ -234,7 +248,7 @@ __global__ void k_mcp_finalize(const double* __restrict__ part, int n, double* _
 // 25 % faster than at 48; the 27-offset pass would spill there and keeps its registers.
 template <int KT>
 __global__ void __launch_bounds__(kBlock, KT == 27 ? 1 : 8) k_mcp_residual(int64_t N, Offsets of, int limiter,
-                                                         const unsigned long long* __restrict__ clip,
+                                                         const MaskWord<KT>* __restrict__ clip,
                                                          const float2* __restrict__ c_up,
                                                          const float2* __restrict__ yp, const uint8_t* __restrict__ dir,
                                                          double* __restrict__ res, double* __restrict__ part) {
@@ -365,6 +379,10 @@ int mc_pair_setup(afc_problem_s* p) {
       (st = p->yp2.alloc(N, p->pad)) ||
       (st = p->cp_up.alloc(p->Kup * N)))
     return st;
+  if (p->K <= 32) {
+    if ((st = p->mask32.alloc(N)) || (st = p->clip32.alloc(N, p->pad))) return st;
+    AFC_LAUNCH(p, "k_mcp_mask32", k_mcp_mask32<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->mask.p, p->mask32.p));
+  }
   AFC_LAUNCH(p, "k_mcp_setup", k_mcp_setup<<<grid_for(N), kBlock, 0, p->stream>>>(
                                    N, p->offs, p->AG.p, p->f.p, p->kij_up.p, p->kji_up.p, p->AGp.p, p->fp2.p,
                                    p->pk_hi.p, p->pk_lo.p));
@@ -387,22 +405,32 @@ int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res
   int st = AFC_OK;
   with_K(p->K, [&](auto kc) {
     constexpr int KT = decltype(kc)::value;
+    using M = MaskWord<KT>;
+    const M* mask;
+    M* clip;
+    if constexpr (std::is_same_v<M, unsigned>) {
+      mask = p->mask32.p;
+      clip = p->clip32.p;
+    } else {
+      mask = p->mask.p;
+      clip = p->clip.p;
+    }
     cudaError_t e;
     AFC_LAUNCH(p, "k_mcp_rows", e = launch_pass(pdl, k_mcp_rows<KT>, dim3((unsigned)g), dim3(kBlock), s, N, p->offs,
-                                                (const unsigned long long*)p->mask.p, (const float2*)p->up2.p,
+                                                mask, (const float2*)p->up2.p,
                                                 (const float2*)p->AGp.p, (const float2*)p->fp2.p, p->yp2.p, p->abh2.p,
-                                                p->abl2.p, p->clip.p));
+                                                p->abl2.p, clip));
     if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_rows"); return; }
     if (limiter == AFC_LIM_MC) {
       AFC_LAUNCH(p, "k_mcp_edges",
                  e = launch_pass(pdl, k_mcp_edges<KT>, dim3((unsigned)grid_for(N, 32)), dim3(32, p->Kup), s, N, p->offs,
                                  (const float2*)p->pk_hi.p, (const float2*)p->pk_lo.p, (const float2*)p->up2.p,
-                                 (const float2*)p->abh2.p, (const float2*)p->abl2.p, p->cp_up.p, p->clip.p));
+                                 (const float2*)p->abh2.p, (const float2*)p->abl2.p, p->cp_up.p, clip));
       if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_edges"); return; }
     }
     AFC_LAUNCH(p, "k_mcp_residual",
                e = launch_pass(pdl, k_mcp_residual<KT>, dim3((unsigned)g), dim3(kBlock), s, N, p->offs, limiter,
-                               (const unsigned long long*)p->clip.p, (const float2*)p->cp_up.p, (const float2*)p->yp2.p,
+                               (const M*)clip, (const float2*)p->cp_up.p, (const float2*)p->yp2.p,
                                (const uint8_t*)p->dir.p, res, p->part.p));
     if (e != cudaSuccess) { st = cuda_fail(e, "launch k_mcp_residual"); return; }
     if (normsq_slot) {
