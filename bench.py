@@ -181,7 +181,7 @@ def _timed_steps(P, opts, steps, flush, stream, torch):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (profiles/k_bicg_fused_q1_65.md), valid while the kernel's sources hash as they did then.
 _NCU_TRAFFIC = {
-    "k_bicg_fused": {"bytes": 83.16e6, "sha1": "c7ec0aa7bee831f1",
+    "k_bicg_fused": {"bytes": 76.80e6, "sha1": "11b039bea6594c49",
                      "sources": ("krylov.cu", "kernels_common.cuh", "afc_internal.h", "grid_sync.cuh")},
 }
 

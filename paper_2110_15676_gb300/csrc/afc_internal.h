@@ -160,7 +160,8 @@ struct afc_problem_s {
   afc::DBuf<float2> up2, yp2;       // node vectors: u and y = f - AG u as pairs
   afc::DBuf<float2> abh2, abl2;     // node vectors: high and low parts of (A, B) = (u_max - u, u - u_min)
   afc::DBuf<float2> cp_up;          // Kup * N: clipped amount of each pair, at its lower row
-  afc::DBuf<unsigned> mask32, clip32;   // node vectors, K <= 32: presence and clip masks in 32 bits
+  afc::DBuf<unsigned> mask32, clip32;   // node vectors, 16 < K <= 32: presence and clip masks in 32 bits
+  afc::DBuf<uint16_t> mask16, clip16;   // K <= 16: the same in 16 bits (clip16: N + 1 entries, no halo)
   afc::DBuf<double> r_up;           // Kup * N: antidiffusive flux of each pair, at its lower row
   // mixed-precision explicit stage: m_ij, d_ij, r_ij (Kup * N) and u, udot^L (node vectors) in single
   afc::DBuf<float> m32_up, d32_up, r32, uf, udf;

@@ -117,7 +117,7 @@ void destroy_all(afc_problem_s* p) {
   p->conn.free_(); p->inc_ptr.free_(); p->inc.free_(); p->mask.free_(); p->dir.free_(); p->clip.free_();
   p->pairf.free_(); p->nodef.free_();
   p->AGp.free_(); p->fp2.free_(); p->pk_hi.free_(); p->pk_lo.free_(); p->up2.free_(); p->yp2.free_(); p->abh2.free_(); p->abl2.free_();
-  p->cp_up.free_(); p->mask32.free_(); p->clip32.free_();
+  p->cp_up.free_(); p->mask32.free_(); p->clip32.free_(); p->mask16.free_(); p->clip16.free_();
   p->m32_up.free_(); p->d32_up.free_(); p->r32.free_(); p->uf.free_(); p->udf.free_();
   if (p->host_scal) cudaFreeHost(p->host_scal);
   delete p;

@@ -221,6 +221,7 @@ struct KrylovWork {
 
 template struct DBuf<char>;
 template struct DBuf<unsigned int>;
+template struct DBuf<uint16_t>;
 
 namespace {
 

@@ -42,16 +42,30 @@ namespace afc {
 
 namespace {
 
-// Word of the per-row presence and clip masks (bit k: offset k): 32 bits when the
-// offsets are known at compile time to number at most 32 (P1: 15, Q1: 27), which
-// halves the masks' traffic and the edge pass's atomics; 64 bits otherwise.
+// Word of the per-row presence and clip masks (bit k: offset k), as narrow as the
+// number of offsets known at compile time allows: 16 bits for P1 (15 offsets), 32
+// for Q1 (27), 64 otherwise; narrower masks mean less traffic in the rows and
+// residual passes.  16-bit clip masks are set by 32-bit atomics on the aligned word
+// that holds two rows' masks (row i in the half (i & 1) of word i >> 1).
 template <int KT>
-using MaskWord = std::conditional_t<(KT > 0 && KT <= 32), unsigned, unsigned long long>;
+using MaskWord = std::conditional_t<(KT > 0 && KT <= 16), uint16_t,
+                                    std::conditional_t<(KT > 0 && KT <= 32), unsigned, unsigned long long>>;
 
-// The presence masks in 32 bits (once, at assembly).
-__global__ void k_mcp_mask32(int64_t N, const unsigned long long* __restrict__ mask, unsigned* __restrict__ m32) {
+// The presence masks in a narrower word (once, at assembly).
+template <class M>
+__global__ void k_mcp_mask_narrow(int64_t N, const unsigned long long* __restrict__ mask, M* __restrict__ m) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < N) m32[i] = (unsigned)mask[i];
+  if (i < N) m[i] = (M)mask[i];
+}
+
+// Sets bit b of row r's clip mask.
+template <class M>
+__device__ __forceinline__ void clip_set(M* clip, int64_t r, int b) {
+  if constexpr (sizeof(M) == 2) {
+    atomicOr(reinterpret_cast<unsigned*>(clip) + (r >> 1), (1u << b) << (16 * (int)(r & 1)));
+  } else {
+    atomicOr(clip + r, (M)1 << b);
+  }
 }
 
 __global__ void k_mcp_split(int64_t N, const double* __restrict__ u, float2* __restrict__ up) {
@@ -231,8 +245,8 @@ __global__ void k_mcp_edges(int64_t N, Offsets of, const float2* __restrict__ pk
     c_up[q] = c;
     // the pair's bit at both ends: offset index Kup + 1 + ku at row i, Kup - 1 - ku
     // (the offset -o back to i) at row j
-    atomicOr(clip + i, (MaskWord<KT>)1 << (Kup + 1 + ku));
-    atomicOr(clip + j, (MaskWord<KT>)1 << (Kup - 1 - ku));
+    clip_set(clip, i, Kup + 1 + ku);
+    clip_set(clip, j, Kup - 1 - ku);
   }
 }
 
@@ -379,9 +393,16 @@ int mc_pair_setup(afc_problem_s* p) {
       (st = p->yp2.alloc(N, p->pad)) ||
       (st = p->cp_up.alloc(p->Kup * N)))
     return st;
-  if (p->K <= 32) {
+  if (p->K <= 16) {
+    // clip16 without a halo and with one entry more, so that it starts 4-byte aligned and
+    // the word holding row N - 1 lies inside it
+    if ((st = p->mask16.alloc(N)) || (st = p->clip16.alloc(N + 1))) return st;
+    AFC_LAUNCH(p, "k_mcp_mask_narrow",
+               k_mcp_mask_narrow<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->mask.p, p->mask16.p));
+  } else if (p->K <= 32) {
     if ((st = p->mask32.alloc(N)) || (st = p->clip32.alloc(N, p->pad))) return st;
-    AFC_LAUNCH(p, "k_mcp_mask32", k_mcp_mask32<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->mask.p, p->mask32.p));
+    AFC_LAUNCH(p, "k_mcp_mask_narrow",
+               k_mcp_mask_narrow<<<grid_for(N), kBlock, 0, p->stream>>>(N, p->mask.p, p->mask32.p));
   }
   AFC_LAUNCH(p, "k_mcp_setup", k_mcp_setup<<<grid_for(N), kBlock, 0, p->stream>>>(
                                    N, p->offs, p->AG.p, p->f.p, p->kij_up.p, p->kji_up.p, p->AGp.p, p->fp2.p,
@@ -408,7 +429,10 @@ int mc_pair_residual(afc_problem_s* p, const double* u, int limiter, double* res
     using M = MaskWord<KT>;
     const M* mask;
     M* clip;
-    if constexpr (std::is_same_v<M, unsigned>) {
+    if constexpr (std::is_same_v<M, uint16_t>) {
+      mask = p->mask16.p;
+      clip = p->clip16.p;
+    } else if constexpr (std::is_same_v<M, unsigned>) {
       mask = p->mask32.p;
       clip = p->clip32.p;
     } else {
